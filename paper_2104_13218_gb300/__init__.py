@@ -1,0 +1,14 @@
+"""GB300-native stochastic Chebyshev (KPM) typicality for spin-1/2 Heisenberg models.
+
+The compute path is libkpm.so (CUDA for sm_103a, C ABI in include/kpm.h);
+this package only marshals arguments (see api.py).
+"""
+from ._lib import KPMError, lib, library_path  # noqa: F401
+from .api import (ChebyshevThermo, CModel, SectorSet, bounds, bounds_workspace_size,  # noqa: F401
+                  chebyshev_thermo, moments, moments_backward, moments_backward_workspace_size,
+                  moments_workspace_size, sector_dims, sector_set, thermo, thermo_backward)
+
+__all__ = ["lib", "library_path", "KPMError", "bounds", "moments", "thermo", "thermo_backward",
+           "moments_backward", "chebyshev_thermo", "ChebyshevThermo", "sector_set", "sector_dims",
+           "bounds_workspace_size", "moments_workspace_size", "moments_backward_workspace_size",
+           "CModel", "SectorSet"]

@@ -1,0 +1,346 @@
+// Spectral bounds of every sector for the rescaling of Eq. E-2-3 / E-2-4,
+// from the Lanczos method the paper uses for extremal energies (Sec. 3.1.2).
+//
+// All sectors run together: two independent Lanczos sequences per sector
+// (start vectors drawn like the moment vectors) stored as 2-value rows
+// (16 bytes per state) in the same stacked layout as the moment loop.  Each
+// iteration is three kernels:
+//   w = H q_j - beta_j q_{j-1}  (written over q_{j-1}),  alpha_j = <w, q_j>
+//   w -= alpha_j q_j,  beta_{j+1} = |w|
+//   q_{j+1} = w / beta_{j+1}
+// with per-tile partial sums reduced in tile order by the last block of each
+// kernel.  The host then finds the extreme eigenvalues of each tridiagonal
+// matrix by Sturm-sequence bisection and widens them by the residual bound
+// |beta_{m+1} y_m| of the Ritz pair (y the Ritz vector of the tridiagonal
+// matrix), which brackets an eigenvalue of H.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kpm_device.cuh"
+#include "kpm_run.h"
+
+namespace kpm {
+
+constexpr int kMaxLanczos = 1000;
+
+struct LanczosArgs {
+  double2 *P;        // q_{j-1} in, w out (kernel 1); w (kernel 2, 3)
+  const double2 *Q;  // q_j
+  TablesDev tb;
+  double *partials;  // [n_tiles][2]
+  double *coef;      // kernel 1: beta_j per [sector][2]; kernel 2: alpha_j; kernel 3: beta_{j+1}
+  double *out;       // kernel 1: alpha_j [sector][2]; kernel 2: beta_{j+1}
+  int *queue, *done;
+  int mode;          // 1 = matvec, 2 = orthogonalise, 3 = normalise
+  double breakdown;  // beta below this ends a sequence
+};
+
+__global__ void __launch_bounds__(kThreads)
+    lanczos_kernel(const __grid_constant__ LanczosArgs a, const __grid_constant__ BondsDev bd) {
+  __shared__ double s_red[kWarps * 2];
+  __shared__ int s_tile, s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.tb.n_tiles) break;
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const double c0 = a.coef[tile.sector * 2], c1 = a.coef[tile.sector * 2 + 1];
+    double acc[2] = {0.0, 0.0};
+    uint32_t hb = tile.b_first;
+    // one state per thread, consecutive states on consecutive lanes
+    for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
+      const int64_t row = tile.row0 + u;
+      if (a.mode == 1) {
+        uint64_t s;
+        if (sd.n_up < 0)
+          s = (uint64_t)(row - sd.row0);
+        else
+          s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+        double d = bd.J_quarter_sum;
+        double h0 = 0.0, h1 = 0.0;
+        for (int b = 0; b < bd.n_bonds; ++b) {
+          const uint64_t m = bd.mask[b];
+          const uint64_t tt = s & m;
+          if (tt != 0 && tt != m) {
+            d -= 0.5 * bd.J[b];
+            const uint64_t f = s ^ m;
+            const int64_t nr = sd.row0 + (sd.n_up < 0 ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+            const double2 v = __ldg(a.Q + nr);
+            h0 = fma(0.5 * bd.J[b], v.x, h0);
+            h1 = fma(0.5 * bd.J[b], v.y, h1);
+          }
+        }
+        const double2 q = a.Q[row];
+        const double2 z = a.P[row];
+        double2 w;
+        w.x = fma(d, q.x, h0) - c0 * z.x;
+        w.y = fma(d, q.y, h1) - c1 * z.y;
+        a.P[row] = w;
+        acc[0] = fma(w.x, q.x, acc[0]);
+        acc[1] = fma(w.y, q.y, acc[1]);
+      } else if (a.mode == 2) {
+        const double2 q = a.Q[row];
+        double2 w = a.P[row];
+        w.x -= c0 * q.x;
+        w.y -= c1 * q.y;
+        a.P[row] = w;
+        acc[0] = fma(w.x, w.x, acc[0]);
+        acc[1] = fma(w.y, w.y, acc[1]);
+      } else {
+        double2 w = a.P[row];
+        w.x = c0 > 0.0 ? w.x / c0 : 0.0;
+        w.y = c1 > 0.0 ? w.y / c1 : 0.0;
+        a.P[row] = w;
+      }
+    }
+    block_sum<2>(acc, s_red);
+    if (threadIdx.x == 0 && a.mode != 3) {
+      a.partials[(int64_t)t * 2] = acc[0];
+      a.partials[(int64_t)t * 2 + 1] = acc[1];
+    }
+  }
+  if (a.mode == 3) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int sec = warp; sec < a.tb.n_sectors; sec += kWarps) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int t = a.tb.tile_begin[sec] + lane; t < a.tb.tile_end[sec]; t += 32) {
+      v0 += __ldcg(a.partials + (int64_t)t * 2);
+      v1 += __ldcg(a.partials + (int64_t)t * 2 + 1);
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      if (a.mode == 1) {
+        a.out[sec * 2] = v0;
+        a.out[sec * 2 + 1] = v1;
+      } else {
+        const double b0 = sqrt(v0), b1 = sqrt(v1);
+        a.out[sec * 2] = b0 > a.breakdown ? b0 : 0.0;
+        a.out[sec * 2 + 1] = b1 > a.breakdown ? b1 : 0.0;
+      }
+    }
+  }
+}
+
+namespace {
+
+// Number of eigenvalues of the m x m tridiagonal (alpha, beta) below x.
+int sturm_count(const std::vector<double> &al, const std::vector<double> &be, int m, double x) {
+  int count = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double b2 = i > 0 ? be[i] * be[i] : 0.0;
+    d = al[i] - x - (i > 0 ? b2 / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++count;
+  }
+  return count;
+}
+
+// k-th smallest eigenvalue (0-based) by bisection.
+double tridiag_eig(const std::vector<double> &al, const std::vector<double> &be, int m, int k) {
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(be[i]) : 0.0) + (i + 1 < m ? std::fabs(be[i + 1]) : 0.0);
+    lo = std::min(lo, al[i] - r);
+    hi = std::max(hi, al[i] + r);
+  }
+  const double scale = std::max({1.0, std::fabs(lo), std::fabs(hi)});
+  for (int it = 0; it < 200 && hi - lo > 4e-16 * scale; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(al, be, m, mid) > k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// |last component| of the unit eigenvector of T for eigenvalue theta, by
+// three steps of inverse iteration, each a tridiagonal solve of
+// (T - sigma) z = y by forward elimination and back substitution.
+double ritz_last_component(const std::vector<double> &al, const std::vector<double> &be, int m,
+                           double theta) {
+  if (m == 1) return 1.0;
+  const double sigma = theta + 1e-13 * std::max(1.0, std::fabs(theta));
+  std::vector<double> y(m, 1.0), cp(m, 0.0), dp(m, 0.0);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i < m; ++i) {
+      double denom = al[i] - sigma - (i > 0 ? be[i] * cp[i - 1] : 0.0);
+      if (std::fabs(denom) < 1e-300) denom = 1e-300;
+      cp[i] = (i + 1 < m) ? be[i + 1] / denom : 0.0;
+      dp[i] = (y[i] - (i > 0 ? be[i] * dp[i - 1] : 0.0)) / denom;
+    }
+    y[m - 1] = dp[m - 1];
+    for (int i = m - 2; i >= 0; --i) y[i] = dp[i] - cp[i] * y[i + 1];
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return 1.0;
+    for (int i = 0; i < m; ++i) y[i] /= nrm;
+  }
+  return std::fabs(y[m - 1]);
+}
+
+int sm_count_b() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(n, 1);
+}
+
+struct BoundsLayout {
+  MomentsRun run;    // plan with R = 2 FP64 rows
+  size_t bytes = 0;
+};
+
+int prepare_bounds(const kpm_model *m, int n_sectors, const int32_t *n_up, BoundsLayout *bl) {
+  KPM_TRY(prepare_run(m, n_sectors, n_up, 2, 2, KPM_FP64, &bl->run));
+  const MomentsRun &r = bl->run;
+  bl->bytes = 2 * r.vec_bytes + tables_bytes(r.plan) +
+              align256(std::max<size_t>(1, r.plan.tiles.size()) * 2 * sizeof(double)) +
+              2 * align256((size_t)(kMaxLanczos + 1) * n_sectors * 2 * sizeof(double)) +
+              align256((size_t)4 * (kMaxLanczos + 1) * sizeof(int)) + 1024;
+  return KPM_OK;
+}
+
+}  // namespace
+
+}  // namespace kpm
+
+using namespace kpm;
+
+extern "C" size_t kpm_bounds_workspace_size(const kpm_model *model, int32_t n_sectors,
+                                            const int32_t *n_up) {
+  BoundsLayout bl;
+  if (prepare_bounds(model, n_sectors, n_up, &bl) != KPM_OK) return 0;
+  return bl.bytes;
+}
+
+extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
+                          double eps, int32_t max_iter, double tol, uint64_t seed, double *a_out,
+                          double *b_out, double *e_min, double *e_max, void *workspace,
+                          size_t ws_bytes, void *stream_ptr) {
+  clear_error();
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+  KPM_REQUIRE(a_out && b_out, KPM_EINVAL, "a and b outputs are required");
+  KPM_REQUIRE(max_iter >= 1 && max_iter <= kMaxLanczos, KPM_EINVAL, "max_iter = %d outside 1..%d",
+              max_iter, kMaxLanczos);
+  KPM_REQUIRE(eps >= 0.0 && eps < 2.0, KPM_EINVAL, "eps = %g outside [0, 2)", eps);
+  BoundsLayout bl;
+  KPM_TRY(prepare_bounds(model, n_sectors, n_up, &bl));
+  MomentsRun &r = bl.run;
+  Workspace ws;
+  KPM_TRY(ws.acquire(workspace, ws_bytes, bl.bytes, stream));
+  Arena arena{reinterpret_cast<char *>(ws.ptr), ws.size, 0};
+  double2 *P = arena.take<double2>(r.vec_bytes / sizeof(double2));
+  double2 *Q = arena.take<double2>(r.vec_bytes / sizeof(double2));
+  double *partials = arena.take<double>(std::max<size_t>(1, r.plan.tiles.size()) * 2);
+  const size_t nab = (size_t)(kMaxLanczos + 1) * n_sectors * 2;
+  double *alpha = arena.take<double>(nab);
+  double *beta = arena.take<double>(nab);
+  int *counters = arena.take<int>((size_t)4 * (kMaxLanczos + 1));
+  KPM_REQUIRE(P && Q && partials && alpha && beta && counters, KPM_ENOMEM,
+              "workspace too small for kpm_bounds");
+  std::vector<SectorDev> sec(n_sectors);
+  for (int i = 0; i < n_sectors; ++i) {
+    sec[i].row0 = r.plan.row0[i];
+    sec[i].dim = r.plan.dim[i];
+    sec[i].n_up = r.plan.n_up[i];
+    sec[i].hb_begin = r.plan.hb_begin[i];
+    sec[i].inv_a = 1.0;
+    sec[i].b = 0.0;
+    sec[i].Mval = 0.0;
+  }
+  KPM_TRY(upload_tables(r.plan, sec, arena, stream, &r.tb));
+  KPM_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4 * (kMaxLanczos + 1), stream));
+  KPM_CUDA(cudaMemsetAsync(beta, 0, sizeof(double) * nab, stream));
+  KPM_CUDA(cudaMemsetAsync(alpha, 0, sizeof(double) * nab, stream));
+  KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));
+  // q_0: normalised random signs, two sequences per sector
+  KPM_TRY(launch_init(r, Q, seed, 0, stream));
+
+  double jabs = 0.0;
+  for (int b = 0; b < model->n_bonds; ++b) jabs += std::fabs(model->J[b]);
+  int per_sm = 0;
+  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kThreads, 0));
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * sm_count_b(), (int64_t)r.plan.tiles.size()));
+  LanczosArgs la;
+  la.tb = r.tb;
+  la.partials = partials;
+  la.breakdown = 1e-12 * std::max(1.0, jabs);
+  for (int j = 0; j < max_iter; ++j) {
+    for (int mode = 1; mode <= 3; ++mode) {
+      la.P = P;
+      la.Q = Q;
+      la.mode = mode;
+      la.queue = counters + 4 * j + (mode == 1 ? 0 : (mode == 2 ? 2 : 0));
+      la.done = la.queue + 1;
+      if (mode == 3) la.queue = counters + 4 * kMaxLanczos;  // reset below
+      la.coef = mode == 1 ? beta + (size_t)j * n_sectors * 2
+                          : (mode == 2 ? alpha + (size_t)j * n_sectors * 2
+                                       : beta + (size_t)(j + 1) * n_sectors * 2);
+      la.out = mode == 1 ? alpha + (size_t)j * n_sectors * 2 : beta + (size_t)(j + 1) * n_sectors * 2;
+      if (mode == 3) KPM_CUDA(cudaMemsetAsync(la.queue, 0, sizeof(int) * 2, stream));
+      void *args[] = {(void *)&la, (void *)&r.bonds};
+      KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
+      count_launches(1);
+    }
+    std::swap(P, Q);  // P = q_j, Q = q_{j+1}
+  }
+  std::vector<double> h_alpha(nab), h_beta(nab);
+  KPM_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * nab, cudaMemcpyDeviceToHost, stream));
+  KPM_CUDA(cudaMemcpyAsync(h_beta.data(), beta, sizeof(double) * nab, cudaMemcpyDeviceToHost, stream));
+  KPM_CUDA(cudaStreamSynchronize(stream));
+
+  int status = KPM_OK;
+  for (int s = 0; s < n_sectors; ++s) {
+    double lo = INFINITY, hi = -INFINITY, worst = 0.0;
+    for (int col = 0; col < 2; ++col) {
+      std::vector<double> al, be;
+      be.push_back(0.0);
+      int m = 0;
+      for (int j = 0; j < max_iter; ++j) {
+        al.push_back(h_alpha[((size_t)j * n_sectors + s) * 2 + col]);
+        ++m;
+        const double bnext = h_beta[((size_t)(j + 1) * n_sectors + s) * 2 + col];
+        if (bnext == 0.0 || m >= r.plan.dim[s]) {
+          be.push_back(0.0);
+          break;
+        }
+        be.push_back(bnext);
+      }
+      // be[i] couples i-1 and i (i >= 1); be[m] is the residual coupling
+      const double bres = be.size() > (size_t)m ? std::fabs(be[m]) : 0.0;
+      const double tmin = tridiag_eig(al, be, m, 0);
+      const double tmax = tridiag_eig(al, be, m, m - 1);
+      const double rmin = bres * ritz_last_component(al, be, m, tmin);
+      const double rmax = bres * ritz_last_component(al, be, m, tmax);
+      lo = std::min(lo, tmin - rmin);
+      hi = std::max(hi, tmax + rmax);
+      worst = std::max({worst, rmin / std::max(1.0, std::fabs(tmin)),
+                        rmax / std::max(1.0, std::fabs(tmax))});
+    }
+    if (worst > tol) status = KPM_ENOTCONV;
+    double m_ = (hi - lo) / (2.0 - eps);
+    const double c_ = 0.5 * (hi + lo);
+    m_ = std::max(m_, 1e-12 * std::max(1.0, std::fabs(c_)));
+    a_out[s] = m_;
+    b_out[s] = c_;
+    if (e_min) e_min[s] = lo;
+    if (e_max) e_max[s] = hi;
+  }
+  if (status == KPM_ENOTCONV)
+    set_error("Lanczos residual bound above tol after %d iterations", max_iter);
+  return status;
+}

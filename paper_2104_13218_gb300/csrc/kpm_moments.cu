@@ -1,0 +1,546 @@
+// The hot loop of the method: stochastic Chebyshev moments (Eq. E-2-6, E-2-7)
+// by the three-term recursion v_{n+1} = 2 H' v_n - v_{n-1} with
+// H' = (H - b)/a (Eq. E-2-3), H the Heisenberg Hamiltonian of Eq. E-3-1-1
+// applied matrix-free on S^z bitstrings.
+//
+// Layout: the R random vectors of a sector are interleaved per basis state
+// (row = state, Rp >= R values per row, 16-byte chunks), all sectors stacked
+// in one array, so one pass over the rows serves every vector and every
+// sector.  One fused kernel per recursion step reads v_n (own row and the
+// rows of the bit-flipped neighbours) and v_{n-1}, writes v_{n+1} over
+// v_{n-1} and produces the two dot products <v_n|v_n> and <v_{n+1}|v_n>
+// (and their M- and M^2-weighted forms for a full-space run) from which
+// mu_{2n} = 2<v_n|v_n> - mu_0 and mu_{2n+1} = 2<v_{n+1}|v_n> - mu_1.
+// Tiles of consecutive states are handed out by a per-step atomic queue to a
+// persistent grid; each tile's partial sums are written to its own slot and
+// the last block to finish reduces them in tile order, so results do not
+// depend on the schedule.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "kpm_device.cuh"
+#include "kpm_run.h"
+
+namespace kpm {
+
+struct StepArgs {
+  const void *x;
+  void *zy;
+  TablesDev tb;
+  double *partials;
+  double *sums;     // this step's [n_sectors][NQ]
+  int *queue;
+  int *done;
+  int Rp, G, gpw, first;
+  double half_n;    // N/2
+};
+
+template <typename T, int CPL, bool FULL>
+__global__ void __launch_bounds__(kThreads)
+    cheb_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd) {
+  using C = Chunk<T>;
+  using V = typename C::type;
+  constexpr int W = C::W;
+  constexpr int NQ = FULL ? 6 : 2;
+  __shared__ T s_aj[kMaxBonds];
+  __shared__ T s_jh[kMaxBonds];
+  __shared__ double s_red[kWarps * NQ];
+  __shared__ int s_tile;
+  __shared__ int s_last;
+
+  const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
+  V *__restrict__ zy = reinterpret_cast<V *>(a.zy);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / a.G, sub = lane - grp * a.G;
+  const bool active = grp < a.gpw;
+  const int64_t crow = a.Rp / W;  // chunks per row
+  const int nb = bd.n_bonds;
+  for (int b = threadIdx.x; b < nb; b += kThreads) s_jh[b] = (T)(0.5 * bd.J[b]);
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.tb.n_tiles) break;
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const double A = (a.first ? 1.0 : 2.0) * sd.inv_a;
+    for (int b = threadIdx.x; b < nb; b += kThreads) s_aj[b] = (T)(A * 0.5 * bd.J[b]);
+    __syncthreads();
+
+    double acc64[NQ];
+    KahanF accf[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc64[q] = 0.0;
+    const T A_t = (T)A, b_t = (T)sd.b;
+    // FULL only adds the M-weighted dot products; each tile decides its own basis
+    const bool full_tile = sd.n_up < 0;
+    uint32_t hb = tile.b_first;
+    if (active) {
+      for (uint32_t u = warp * a.gpw + grp; u < tile.count; u += kWarps * a.gpw) {
+        const int64_t row = tile.row0 + u;
+        uint64_t s;
+        if (full_tile)
+          s = (uint64_t)(row - sd.row0);
+        else
+          s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+        T d = (T)bd.J_quarter_sum;
+        V acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = V{};
+        for (int b0 = 0; b0 < nb; b0 += 8) {
+          int64_t nrow[8];
+          bool fl[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int b = b0 + j;
+            fl[j] = false;
+            nrow[j] = 0;
+            if (b < nb) {
+              const uint64_t m = bd.mask[b];
+              const uint64_t tt = s & m;
+              if (tt != 0 && tt != m) {
+                fl[j] = true;
+                d -= s_jh[b];
+                const uint64_t f = s ^ m;
+                nrow[j] = sd.row0 + (full_tile ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (fl[j]) {
+              const T aj = s_aj[b0 + j];
+              const V *src = x + nrow[j] * crow + sub;
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) {
+                const V v = __ldg(src + c * a.G);
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+                  C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
+              }
+            }
+          }
+        }
+        const T ad = A_t * (d - b_t);
+        const V *xo = x + row * crow + sub;
+        V *zo = zy + row * crow + sub;
+        T pxx = 0, pyx = 0;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const V xv = xo[c * a.G];
+          V zv = V{};
+          if (!a.first) zv = __ldcs(zo + c * a.G);
+          V y;
+#pragma unroll
+          for (int e = 0; e < W; ++e) {
+            const T xe = C::get(xv, e);
+            const T ye = fma(ad, xe, C::get(acc[c], e)) - C::get(zv, e);
+            C::set(y, e, ye);
+            pxx = fma(xe, xe, pxx);
+            pyx = fma(ye, xe, pyx);
+          }
+          zo[c * a.G] = y;
+        }
+        if constexpr (sizeof(T) == 8) {
+          acc64[0] += pxx;
+          acc64[1] += pyx;
+          if (FULL) {
+            const double M = (double)__popcll(s) - a.half_n;
+            acc64[2] += M * pxx;
+            acc64[3] += M * pyx;
+            acc64[4] += M * M * pxx;
+            acc64[5] += M * M * pyx;
+          }
+        } else {
+          accf[0].add(pxx);
+          accf[1].add(pyx);
+          if (FULL) {
+            const float M = (float)__popcll(s) - (float)a.half_n;
+            accf[2].add(M * pxx);
+            accf[3].add(M * pyx);
+            accf[4].add(M * M * pxx);
+            accf[5].add(M * M * pyx);
+          }
+        }
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc64[q] = accf[q].value();
+    }
+    block_sum<NQ>(acc64, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) a.partials[(int64_t)t * NQ + q] = acc64[q];
+    }
+  }
+
+  // The last block to finish sums the tile partials of every sector in tile order.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int sec = warp; sec < a.tb.n_sectors; sec += kWarps) {
+      const int t0 = a.tb.tile_begin[sec], t1 = a.tb.tile_end[sec];
+      double v[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+      for (int t = t0 + lane; t < t1; t += 32) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] += __ldcg(a.partials + (int64_t)t * NQ + q);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a.sums[sec * NQ + q] = v[q];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- random vectors
+
+struct InitArgs {
+  void *v0;
+  TablesDev tb;
+  uint64_t seed, r0;
+  int R, Rp, G, gpw;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) init_vectors_kernel(const __grid_constant__ InitArgs a) {
+  using C = Chunk<T>;
+  using V = typename C::type;
+  constexpr int W = C::W;
+  __shared__ uint64_t s_hr[512];
+  const uint64_t hs = splitmix64(a.seed);
+  for (int col = threadIdx.x; col < a.R; col += kThreads) s_hr[col] = splitmix64(hs ^ (a.r0 + (uint64_t)col));
+  __syncthreads();
+  V *v = reinterpret_cast<V *>(a.v0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / a.G, sub = lane - grp * a.G;
+  if (grp >= a.gpw) return;
+  const int crow = a.Rp / W;
+  for (int t = blockIdx.x; t < a.tb.n_tiles; t += gridDim.x) {
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const T norm = (T)(1.0 / sqrt((double)sd.dim));
+    uint32_t hb = tile.b_first;
+    for (uint32_t u = warp * a.gpw + grp; u < tile.count; u += kWarps * a.gpw) {
+      const int64_t row = tile.row0 + u;
+      uint64_t s;
+      if (sd.n_up < 0)
+        s = (uint64_t)(row - sd.row0);
+      else
+        s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+      for (int ch = sub; ch < crow; ch += a.G) {
+        V val;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+          const int col = ch * W + e;
+          T x = 0;
+          if (col < a.R) x = (splitmix64(s_hr[col] ^ s) >> 63) ? -norm : norm;
+          C::set(val, e, x);
+        }
+        v[row * crow + ch] = val;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- moments
+
+struct AssembleArgs {
+  const double *sums;  // [S][n_sectors][NQ]
+  const SectorDev *sectors;
+  double *mu, *mu_M, *mu_M2;
+  int *flag;
+  int n_sectors, K, NQ;
+  double inv_R;
+};
+
+__global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) {
+  const int total = a.n_sectors * a.K;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int sec = i / a.K, n = i - sec * a.K;
+    const int step = n / 2;
+    const bool odd = n & 1;
+    const int nq_out = a.mu_M ? 3 : 1;
+    const bool full = a.sectors[sec].n_up < 0;
+    for (int q = 0; q < 3; ++q) {
+      double *out = q == 0 ? a.mu : (q == 1 ? a.mu_M : a.mu_M2);
+      if (!out) continue;
+      double val;
+      if (full || q == 0) {
+        const int qq = 2 * q + (odd ? 1 : 0);
+        const double raw = a.sums[((int64_t)step * a.n_sectors + sec) * a.NQ + qq] * a.inv_R;
+        if (step == 0) {
+          val = raw;
+        } else {
+          const double base = a.sums[(int64_t)sec * a.NQ + qq] * a.inv_R;  // mu_0 or mu_1
+          val = 2.0 * raw - base;
+        }
+      } else {
+        // a sector: M and M^2 are constants, mu_M = M mu, mu_M2 = M^2 mu
+        const int qq = odd ? 1 : 0;
+        const double raw = a.sums[((int64_t)step * a.n_sectors + sec) * a.NQ + qq] * a.inv_R;
+        const double base = a.sums[(int64_t)sec * a.NQ + qq] * a.inv_R;
+        const double m0 = step == 0 ? raw : 2.0 * raw - base;
+        const double M = a.sectors[sec].Mval;
+        val = (q == 1 ? M : M * M) * m0;
+      }
+      out[(int64_t)sec * a.K + n] = val;
+      if (q == 0 && !(fabs(val) <= 1.0 + 1e-6)) atomicOr(a.flag, 1);
+    }
+    (void)nq_out;
+  }
+}
+
+// ---------------------------------------------------------------- host driver
+
+namespace {
+
+using StepFn = void (*)(const StepArgs, const BondsDev);
+
+template <typename T, int CPL, bool FULL>
+void *step_ptr() {
+  return reinterpret_cast<void *>(&cheb_step_kernel<T, CPL, FULL>);
+}
+
+void *pick_step(int precision, int cpl, bool full) {
+  if (precision == KPM_FP32) {
+    switch (cpl) {
+      case 1: return full ? step_ptr<float, 1, true>() : step_ptr<float, 1, false>();
+      case 2: return full ? step_ptr<float, 2, true>() : step_ptr<float, 2, false>();
+      case 3: return full ? step_ptr<float, 3, true>() : step_ptr<float, 3, false>();
+      default: return full ? step_ptr<float, 4, true>() : step_ptr<float, 4, false>();
+    }
+  }
+  switch (cpl) {
+    case 1: return full ? step_ptr<double, 1, true>() : step_ptr<double, 1, false>();
+    case 2: return full ? step_ptr<double, 2, true>() : step_ptr<double, 2, false>();
+    case 3: return full ? step_ptr<double, 3, true>() : step_ptr<double, 3, false>();
+    default: return full ? step_ptr<double, 4, true>() : step_ptr<double, 4, false>();
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
+                int precision, MomentsRun *run) {
+  KPM_TRY(validate_model(m));
+  KPM_TRY(validate_sectors(m, n_sectors, n_up));
+  KPM_REQUIRE(K >= 2 && (K % 2) == 0, KPM_EINVAL, "n_moments = %d must be even and >= 2", K);
+  KPM_TRY(make_layout(R, precision, &run->lay));
+  run->precision = precision;
+  run->K = K;
+  run->S = K / 2;
+  int64_t rows = 0;
+  bool full = false;
+  for (int s = 0; s < n_sectors; ++s) {
+    rows += kpm_sector_dim(m->n_sites, n_up[s]);
+    full |= n_up[s] < 0;
+  }
+  KPM_TRY(build_plan(m, n_sectors, n_up, choose_tile_states(run->lay.gpw, rows), &run->plan));
+  run->NQ = run->plan.any_full ? 6 : 2;
+  fill_bonds(m, &run->bonds);
+  run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);
+  (void)full;
+  return KPM_OK;
+}
+
+size_t run_bytes(const MomentsRun &r) {
+  return 2 * r.vec_bytes + tables_bytes(r.plan) +
+         align256(r.plan.tiles.size() * r.NQ * sizeof(double)) +
+         align256((size_t)r.S * r.plan.n_sectors * r.NQ * sizeof(double)) +
+         align256((size_t)2 * r.S * sizeof(int)) + 256;
+}
+
+int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cudaStream_t s) {
+  r.vA = arena.take<char>(r.vec_bytes);
+  r.vB = arena.take<char>(r.vec_bytes);
+  r.partials = arena.take<double>(std::max<size_t>(1, r.plan.tiles.size() * r.NQ));
+  r.sums = arena.take<double>((size_t)r.S * r.plan.n_sectors * r.NQ);
+  r.counters = arena.take<int>((size_t)2 * r.S);
+  r.flag = arena.take<int>(1);
+  KPM_REQUIRE(r.vA && r.vB && r.partials && r.sums && r.counters && r.flag, KPM_ENOMEM,
+              "workspace too small for the moment run");
+  std::vector<SectorDev> sec(r.plan.n_sectors);
+  for (int i = 0; i < r.plan.n_sectors; ++i) {
+    KPM_REQUIRE(a[i] > 0.0 && std::isfinite(a[i]) && std::isfinite(b[i]), KPM_EINVAL,
+                "sector %d: rescaling a = %g, b = %g (need a > 0, finite)", i, a[i], b[i]);
+    sec[i].row0 = r.plan.row0[i];
+    sec[i].dim = r.plan.dim[i];
+    sec[i].n_up = r.plan.n_up[i];
+    sec[i].hb_begin = r.plan.hb_begin[i];
+    sec[i].inv_a = 1.0 / a[i];
+    sec[i].b = b[i];
+    sec[i].Mval = r.plan.n_up[i] < 0 ? 0.0 : r.plan.n_up[i] - 0.5 * r.plan.N;
+  }
+  KPM_TRY(upload_tables(r.plan, sec, arena, s, &r.tb));
+  KPM_CUDA(cudaMemsetAsync(r.counters, 0, sizeof(int) * 2 * r.S, s));
+  KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
+  void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
+  int per_sm = 0;
+  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+  per_sm = std::max(per_sm, 1);
+  r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), (int64_t)r.plan.tiles.size());
+  r.grid = std::max(r.grid, 1);
+  return KPM_OK;
+}
+
+int launch_init(const MomentsRun &r, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s) {
+  InitArgs a;
+  a.v0 = v0;
+  a.tb = r.tb;
+  a.seed = seed;
+  a.r0 = r0;
+  a.R = r.lay.R;
+  a.Rp = r.lay.Rp;
+  a.G = r.lay.G;
+  a.gpw = r.lay.gpw;
+  const int grid = (int)std::min<int64_t>((int64_t)r.plan.tiles.size(), (int64_t)8 * sm_count());
+  if (r.precision == KPM_FP32)
+    init_vectors_kernel<float><<<grid, kThreads, 0, s>>>(a);
+  else
+    init_vectors_kernel<double><<<grid, kThreads, 0, s>>>(a);
+  KPM_CUDA(cudaGetLastError());
+  count_launches(1);
+  return KPM_OK;
+}
+
+int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int step, cudaStream_t s) {
+  StepArgs a;
+  a.x = x;
+  a.zy = zy;
+  a.tb = r.tb;
+  a.partials = r.partials;
+  a.sums = r.sums + (size_t)step * r.plan.n_sectors * r.NQ;
+  a.queue = r.counters + 2 * step;
+  a.done = r.counters + 2 * step + 1;
+  a.Rp = r.lay.Rp;
+  a.G = r.lay.G;
+  a.gpw = r.lay.gpw;
+  a.first = first;
+  a.half_n = 0.5 * r.plan.N;
+  void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
+  void *args[] = {(void *)&a, (void *)&r.bonds};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool prof = profiling();
+  if (prof) {
+    KPM_CUDA(cudaEventCreate(&e0));
+    KPM_CUDA(cudaEventCreate(&e1));
+    KPM_CUDA(cudaEventRecord(e0, s));
+  }
+  KPM_CUDA(cudaLaunchKernel(fn, dim3(r.grid), dim3(kThreads), args, 0, s));
+  count_launches(1);
+  if (prof) {
+    KPM_CUDA(cudaEventRecord(e1, s));
+    profile_push(e0, e1);
+  }
+  return KPM_OK;
+}
+
+int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2, cudaStream_t s) {
+  AssembleArgs a;
+  a.sums = r.sums;
+  a.sectors = r.tb.sectors;
+  a.mu = mu;
+  a.mu_M = mu_M;
+  a.mu_M2 = mu_M2;
+  a.flag = r.flag;
+  a.n_sectors = r.plan.n_sectors;
+  a.K = r.K;
+  a.NQ = r.NQ;
+  a.inv_R = 1.0 / r.lay.R;
+  const int total = r.plan.n_sectors * r.K;
+  assemble_kernel<<<(total + 255) / 256, 256, 0, s>>>(a);
+  KPM_CUDA(cudaGetLastError());
+  count_launches(1);
+  return KPM_OK;
+}
+
+}  // namespace kpm
+
+using namespace kpm;
+
+extern "C" size_t kpm_moments_workspace_size(const kpm_model *model, int32_t n_sectors,
+                                             const int32_t *n_up, int32_t n_moments, int32_t R,
+                                             int32_t precision) {
+  MomentsRun run;
+  if (prepare_run(model, n_sectors, n_up, n_moments, R, precision, &run) != KPM_OK) return 0;
+  return run_bytes(run);
+}
+
+extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
+                           const double *a, const double *b, double eps, int32_t n_moments,
+                           int32_t R, uint64_t seed, uint64_t r0, int32_t precision, double *mu,
+                           double *mu_M, double *mu_M2, int32_t on_device, void *workspace,
+                           size_t ws_bytes, void *stream_ptr) {
+  clear_error();
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
+  KPM_REQUIRE(mu != nullptr, KPM_EINVAL, "mu is NULL");
+  MomentsRun run;
+  KPM_TRY(prepare_run(model, n_sectors, n_up, n_moments, R, precision, &run));
+  std::vector<double> av, bv;
+  if (a == nullptr || b == nullptr) {
+    av.resize(n_sectors);
+    bv.resize(n_sectors);
+    int rc = kpm_bounds(model, n_sectors, n_up, eps, 100, 1e-8, splitmix64(seed ^ 0x5EEDB0D5ull),
+                        av.data(), bv.data(), nullptr, nullptr, nullptr, 0, stream_ptr);
+    if (rc != KPM_OK && rc != KPM_ENOTCONV) return rc;
+    a = av.data();
+    b = bv.data();
+  }
+  const size_t out_bytes = align256((size_t)n_sectors * n_moments * sizeof(double));
+  const size_t need = run_bytes(run) + (on_device ? 0 : 3 * out_bytes);
+  Workspace ws;
+  KPM_TRY(ws.acquire(workspace, ws_bytes, need, stream));
+  Arena arena{reinterpret_cast<char *>(ws.ptr), ws.size, 0};
+  KPM_TRY(setup_run(run, a, b, arena, stream));
+  double *dmu = mu, *dmuM = mu_M, *dmuM2 = mu_M2;
+  if (!on_device) {
+    dmu = arena.take<double>((size_t)n_sectors * n_moments);
+    dmuM = mu_M ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
+    dmuM2 = mu_M2 ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
+    KPM_REQUIRE(dmu && (!mu_M || dmuM) && (!mu_M2 || dmuM2), KPM_ENOMEM, "workspace too small");
+  }
+  KPM_TRY(launch_init(run, run.vA, seed, r0, stream));
+  KPM_TRY(launch_step(run, run.vA, run.vB, 1, 0, stream));
+  void *x = run.vB, *zy = run.vA;
+  for (int step = 1; step < run.S; ++step) {
+    KPM_TRY(launch_step(run, x, zy, 0, step, stream));
+    std::swap(x, zy);
+  }
+  KPM_TRY(launch_assemble(run, dmu, dmuM, dmuM2, stream));
+  const size_t nbytes = (size_t)n_sectors * n_moments * sizeof(double);
+  if (!on_device) {
+    KPM_CUDA(cudaMemcpyAsync(mu, dmu, nbytes, cudaMemcpyDeviceToHost, stream));
+    if (mu_M) KPM_CUDA(cudaMemcpyAsync(mu_M, dmuM, nbytes, cudaMemcpyDeviceToHost, stream));
+    if (mu_M2) KPM_CUDA(cudaMemcpyAsync(mu_M2, dmuM2, nbytes, cudaMemcpyDeviceToHost, stream));
+  }
+  int flag = 0;
+  KPM_CUDA(cudaMemcpyAsync(&flag, run.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  KPM_CUDA(cudaStreamSynchronize(stream));
+  if (flag) {
+    set_error("some |mu_n| > 1 + 1e-6: the rescaled spectrum leaves [-1, 1]");
+    return KPM_EBOUNDS;
+  }
+  return KPM_OK;
+}

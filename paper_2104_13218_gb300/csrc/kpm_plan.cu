@@ -1,0 +1,346 @@
+// Host side of libkpm: argument checks, the split combinadic rank tables of
+// the S^z sectors (Sec. 2: the basis is decomposed by total magnetisation M,
+// sector = states with N/2 + M up spins), the tile list of a launch, the
+// workspace and the row layout of the interleaved random vectors.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+namespace {
+thread_local char g_error[1024] = "";
+}
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_error, sizeof(g_error), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_error[0] = '\0'; }
+
+const char *last_error() { return g_error; }
+
+int64_t binom(int n, int k) {
+  if (k < 0 || n < 0 || k > n) return 0;
+  if (k > n - k) k = n - k;
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (unsigned)(n - k + i) / (unsigned)i;
+  return (int64_t)r;
+}
+
+int validate_model(const kpm_model *m) {
+  KPM_REQUIRE(m != nullptr, KPM_EINVAL, "model is NULL");
+  KPM_REQUIRE(m->n_sites >= 1 && m->n_sites <= kMaxSites, KPM_EINVAL,
+              "n_sites = %d outside 1..%d", m->n_sites, kMaxSites);
+  KPM_REQUIRE(m->n_bonds >= 0 && m->n_bonds <= kMaxBonds, KPM_EINVAL,
+              "n_bonds = %d outside 0..%d", m->n_bonds, kMaxBonds);
+  if (m->n_bonds > 0)
+    KPM_REQUIRE(m->bi && m->bj && m->J, KPM_EINVAL, "bond arrays are NULL");
+  for (int b = 0; b < m->n_bonds; ++b) {
+    KPM_REQUIRE(m->bi[b] >= 0 && m->bi[b] < m->n_sites && m->bj[b] >= 0 &&
+                    m->bj[b] < m->n_sites && m->bi[b] != m->bj[b],
+                KPM_EINVAL, "bond %d = (%d, %d) is not a pair of distinct sites", b, m->bi[b],
+                m->bj[b]);
+  }
+  return KPM_OK;
+}
+
+int validate_sectors(const kpm_model *m, int n_sectors, const int32_t *n_up) {
+  KPM_REQUIRE(n_sectors >= 1 && n_up != nullptr, KPM_EINVAL, "need at least one sector");
+  for (int s = 0; s < n_sectors; ++s)
+    KPM_REQUIRE(n_up[s] >= -1 && n_up[s] <= m->n_sites, KPM_EINVAL,
+                "n_up[%d] = %d outside -1..%d", s, n_up[s], m->n_sites);
+  return KPM_OK;
+}
+
+int64_t choose_tile_states(int gpw, int64_t total_rows) {
+  // 64 block iterations of kWarps * gpw states, but at least ~4 tiles per SM
+  // for small problems (152 SMs).
+  int64_t big = (int64_t)64 * kWarps * gpw;
+  int64_t small = std::max<int64_t>((int64_t)kWarps * gpw, total_rows / (4 * 152));
+  return std::max<int64_t>(1, std::min(big, small));
+}
+
+int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t tile_states,
+               Plan *p) {
+  KPM_TRY(validate_model(m));
+  KPM_TRY(validate_sectors(m, n_sectors, n_up));
+  KPM_REQUIRE(tile_states >= 1, KPM_EINVAL, "tile_states < 1");
+  const int N = m->n_sites;
+  p->N = N;
+  p->L = N / 2;
+  p->H = N - p->L;
+  p->n_sectors = n_sectors;
+  p->n_up.assign(n_up, n_up + n_sectors);
+  p->dim.resize(n_sectors);
+  p->row0.resize(n_sectors);
+  p->any_full = p->any_sector = false;
+  int64_t rows = 0;
+  for (int s = 0; s < n_sectors; ++s) {
+    p->dim[s] = n_up[s] < 0 ? ((int64_t)1 << N) : binom(N, n_up[s]);
+    p->row0[s] = rows;
+    rows += p->dim[s];
+    if (n_up[s] < 0)
+      p->any_full = true;
+    else
+      p->any_sector = true;
+  }
+  p->total_rows = rows;
+  p->tile_states = tile_states;
+
+  const int L = p->L, H = p->H;
+  const uint32_t nlo = 1u << L, nhi = 1u << H;
+  p->lo_rank.clear();
+  p->hi_rank.clear();
+  p->lo_list.clear();
+  p->lo_start.clear();
+  p->hb_hi.clear();
+  p->hb_off.clear();
+  p->hb_begin.assign(n_sectors, 0);
+  if (p->any_sector) {
+    // low part: colex rank of the low bits among patterns of equal popcount
+    p->lo_rank.resize(nlo);
+    std::vector<uint32_t> count(L + 2, 0);
+    for (uint32_t lo = 0; lo < nlo; ++lo) {
+      uint64_t r = 0;
+      int j = 0;
+      for (int q = 0; q < L; ++q)
+        if ((lo >> q) & 1u) r += (uint64_t)binom(q, ++j);
+      p->lo_rank[lo] = (uint32_t)r;
+      count[__builtin_popcount(lo)]++;
+    }
+    p->lo_start.assign(L + 2, 0);
+    for (int c = 0; c <= L; ++c) p->lo_start[c + 1] = p->lo_start[c] + count[c];
+    p->lo_list.resize(nlo);
+    std::vector<uint32_t> fill(p->lo_start.begin(), p->lo_start.end());
+    for (uint32_t lo = 0; lo < nlo; ++lo) p->lo_list[fill[__builtin_popcount(lo)]++] = lo;
+    // high part given c set bits below it
+    p->hi_rank.resize((size_t)(L + 1) * nhi);
+    for (int c = 0; c <= L; ++c)
+      for (uint32_t hi = 0; hi < nhi; ++hi) {
+        uint64_t r = 0;
+        int j = c;
+        for (int q = 0; q < H; ++q)
+          if ((hi >> q) & 1u) r += (uint64_t)binom(L + q, ++j);
+        p->hi_rank[(size_t)c * nhi + hi] = (uint32_t)r;
+      }
+    // hi-blocks of every sector in increasing order of the high pattern
+    for (int s = 0; s < n_sectors; ++s) {
+      p->hb_begin[s] = (int32_t)p->hb_hi.size();
+      if (n_up[s] < 0) continue;
+      int64_t covered = 0;
+      for (uint32_t hi = 0; hi < nhi; ++hi) {
+        int c = n_up[s] - __builtin_popcount(hi);
+        if (c < 0 || c > L) continue;
+        p->hb_hi.push_back(hi);
+        p->hb_off.push_back(p->hi_rank[(size_t)c * nhi + hi]);
+        covered += binom(L, c);
+      }
+      KPM_REQUIRE(covered == p->dim[s], KPM_EINVAL, "internal: sector %d blocks cover %lld of %lld",
+                  s, (long long)covered, (long long)p->dim[s]);
+    }
+  }
+  // tiles
+  p->tiles.clear();
+  p->tile_begin.assign(n_sectors, 0);
+  p->tile_end.assign(n_sectors, 0);
+  for (int s = 0; s < n_sectors; ++s) {
+    p->tile_begin[s] = (int32_t)p->tiles.size();
+    int32_t hb0 = p->hb_begin[s];
+    int32_t hb1 = (n_up[s] < 0) ? hb0
+                                : ((s + 1 < n_sectors) ? p->hb_begin[s + 1] : (int32_t)p->hb_hi.size());
+    // hb_begin of later sectors is set above; for the last sector use the array end
+    for (int64_t r0 = 0; r0 < p->dim[s]; r0 += tile_states) {
+      Tile t;
+      t.row0 = p->row0[s] + r0;
+      t.rank0 = (uint32_t)r0;
+      t.count = (uint32_t)std::min<int64_t>(tile_states, p->dim[s] - r0);
+      t.sector = s;
+      t.pad = 0;
+      t.b_first = t.b_last = 0;
+      if (n_up[s] >= 0) {
+        auto first = p->hb_off.begin() + hb0, last = p->hb_off.begin() + hb1;
+        uint32_t a = (uint32_t)r0, z = (uint32_t)(r0 + t.count - 1);
+        t.b_first = (uint32_t)((std::upper_bound(first, last, a) - p->hb_off.begin()) - 1);
+        t.b_last = (uint32_t)((std::upper_bound(first, last, z) - p->hb_off.begin()) - 1);
+      }
+      p->tiles.push_back(t);
+    }
+    p->tile_end[s] = (int32_t)p->tiles.size();
+  }
+  KPM_REQUIRE(p->tiles.size() < (size_t)INT32_MAX, KPM_EINVAL, "too many tiles");
+  return KPM_OK;
+}
+
+void fill_bonds(const kpm_model *m, BondsDev *out) {
+  std::memset(out, 0, sizeof(*out));
+  out->n_bonds = m->n_bonds;
+  out->n_sites = m->n_sites;
+  double q = 0.0;
+  for (int b = 0; b < m->n_bonds; ++b) {
+    out->mask[b] = (1ull << m->bi[b]) | (1ull << m->bj[b]);
+    out->J[b] = m->J[b];
+    q += 0.25 * m->J[b];
+  }
+  out->J_quarter_sum = q;
+}
+
+size_t tables_bytes(const Plan &p) {
+  return align256(p.lo_rank.size() * 4) + align256(p.hi_rank.size() * 4) +
+         align256(p.lo_list.size() * 4) + align256(p.lo_start.size() * 4) +
+         align256(p.hb_hi.size() * 4) + align256(p.hb_off.size() * 4) +
+         align256(p.tiles.size() * sizeof(Tile)) +
+         align256((size_t)p.n_sectors * sizeof(SectorDev)) +
+         2 * align256((size_t)p.n_sectors * 4) + 256 * 8;
+}
+
+namespace {
+template <typename T>
+int put(Arena &a, const std::vector<T> &v, cudaStream_t s, const T **out) {
+  size_t n = std::max<size_t>(v.size(), 1);
+  T *d = a.take<T>(n);
+  KPM_REQUIRE(d != nullptr, KPM_ENOMEM, "workspace too small for the basis tables");
+  if (!v.empty()) KPM_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = d;
+  return KPM_OK;
+}
+}  // namespace
+
+int upload_tables(const Plan &p, const std::vector<SectorDev> &sectors, Arena &arena,
+                  cudaStream_t s, TablesDev *t) {
+  KPM_TRY(put(arena, p.lo_rank, s, &t->lo_rank));
+  KPM_TRY(put(arena, p.hi_rank, s, &t->hi_rank));
+  KPM_TRY(put(arena, p.lo_list, s, &t->lo_list));
+  KPM_TRY(put(arena, p.lo_start, s, &t->lo_start));
+  KPM_TRY(put(arena, p.hb_hi, s, &t->hb_hi));
+  KPM_TRY(put(arena, p.hb_off, s, &t->hb_off));
+  KPM_TRY(put(arena, p.tiles, s, &t->tiles));
+  KPM_TRY(put(arena, sectors, s, &t->sectors));
+  KPM_TRY(put(arena, p.tile_begin, s, &t->tile_begin));
+  KPM_TRY(put(arena, p.tile_end, s, &t->tile_end));
+  t->n_tiles = (int32_t)p.tiles.size();
+  t->n_sectors = p.n_sectors;
+  t->N = p.N;
+  t->L = p.L;
+  t->H = p.H;
+  t->pad = 0;
+  return KPM_OK;
+}
+
+int Workspace::acquire(void *user, size_t user_bytes, size_t need, cudaStream_t s) {
+  stream = s;
+  if (user != nullptr) {
+    KPM_REQUIRE(user_bytes >= need, KPM_ENOMEM, "workspace of %zu bytes, need %zu", user_bytes,
+                need);
+    KPM_REQUIRE(((uintptr_t)user & 255) == 0, KPM_EINVAL, "workspace not 256-byte aligned");
+    ptr = user;
+    size = user_bytes;
+    owned = false;
+    return KPM_OK;
+  }
+  size_t free_b = 0, total_b = 0;
+  KPM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  KPM_REQUIRE(need <= free_b, KPM_ENOMEM, "need %zu bytes of device memory, %zu free", need,
+              free_b);
+  KPM_CUDA(cudaMallocAsync(&ptr, need, s));
+  size = need;
+  owned = true;
+  return KPM_OK;
+}
+
+Workspace::~Workspace() {
+  if (owned && ptr) {
+    cudaFreeAsync(ptr, stream);
+    cudaStreamSynchronize(stream);
+  }
+}
+
+int make_layout(int R, int precision, RowLayout *o) {
+  KPM_REQUIRE(precision == KPM_FP64 || precision == KPM_FP32, KPM_EINVAL, "precision %d",
+              precision);
+  KPM_REQUIRE(R >= 1, KPM_EINVAL, "R = %d < 1", R);
+  o->R = R;
+  o->vec_width = precision == KPM_FP32 ? 4 : 2;
+  o->elem = precision == KPM_FP32 ? 4 : 8;
+  o->chunks = (R + o->vec_width - 1) / o->vec_width;
+  o->cpl = (o->chunks + 31) / 32;
+  KPM_REQUIRE(o->cpl <= 4, KPM_EINVAL, "R = %d too large (max %d)", R, 128 * o->vec_width);
+  o->G = (o->chunks + o->cpl - 1) / o->cpl;
+  o->gpw = 32 / o->G;
+  o->Rp = o->G * o->cpl * o->vec_width;
+  return KPM_OK;
+}
+
+namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<bool> g_profiling{false};
+std::mutex g_prof_mutex;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_events;
+}  // namespace
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool profiling() { return g_profiling.load(std::memory_order_relaxed); }
+
+void profile_push(cudaEvent_t start, cudaEvent_t stop) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  g_events.emplace_back(start, stop);
+}
+
+}  // namespace kpm
+
+extern "C" {
+
+int kpm_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lock(kpm::g_prof_mutex);
+  if (on) {
+    for (auto &e : kpm::g_events) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    kpm::g_events.clear();
+  }
+  kpm::g_profiling.store(on != 0);
+  return KPM_OK;
+}
+
+int kpm_profile_read(double *step_ms_total, int64_t *step_launches, int64_t *kernel_launches) {
+  std::lock_guard<std::mutex> lock(kpm::g_prof_mutex);
+  double total = 0.0;
+  int rc = KPM_OK;
+  for (auto &e : kpm::g_events) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.second) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess)
+      rc = KPM_ECUDA;
+    total += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (step_ms_total) *step_ms_total = total;
+  if (step_launches) *step_launches = (int64_t)kpm::g_events.size();
+  if (kernel_launches) *kernel_launches = kpm::g_launches.load();
+  kpm::g_events.clear();
+  if (rc != KPM_OK) kpm::set_error("kpm_profile_read: event query failed");
+  return rc;
+}
+
+int kpm_version(void) { return KPM_VERSION; }
+
+const char *kpm_last_error(void) { return kpm::last_error(); }
+
+int64_t kpm_sector_dim(int32_t n_sites, int32_t n_up) {
+  if (n_sites < 1 || n_sites > kpm::kMaxSites || n_up < -1 || n_up > n_sites) return -1;
+  return n_up < 0 ? ((int64_t)1 << n_sites) : kpm::binom(n_sites, n_up);
+}
+
+}  // extern "C"

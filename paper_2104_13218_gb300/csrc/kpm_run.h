@@ -1,0 +1,44 @@
+// Driver of the Chebyshev moment loop shared by kpm_moments and the adjoint.
+#pragma once
+
+#include "kpm_internal.h"
+
+namespace kpm {
+
+// Everything one forward run needs on the device.
+struct MomentsRun {
+  Plan plan;
+  RowLayout lay;
+  BondsDev bonds;
+  TablesDev tb;
+  int precision = KPM_FP64;
+  int K = 0, S = 0;        // moments, matrix-vector products (S = K/2)
+  int NQ = 2;              // dot products per step: 2, or 6 with a full-space sector
+  int grid = 0;            // persistent grid of the step kernel
+  size_t vec_bytes = 0;    // one interleaved vector (all sectors)
+  void *vA = nullptr, *vB = nullptr;
+  double *partials = nullptr;  // [n_tiles][NQ]
+  double *sums = nullptr;      // [S][n_sectors][NQ]
+  int *counters = nullptr;     // [2*S]: tile queue and finished-block count per step
+  int *flag = nullptr;         // EBOUNDS flag
+};
+
+// Builds the plan and the layout; no device work.
+int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
+                int precision, MomentsRun *run);
+// Device bytes of the run's vectors (2), tables, partials, sums and counters.
+size_t run_bytes(const MomentsRun &run);
+// Carves the run's buffers from the arena and uploads tables (a, b per sector).
+int setup_run(MomentsRun &run, const double *a, const double *b, Arena &arena,
+              cudaStream_t stream);
+// v0 <- random vectors r0 .. r0+R-1 (padding columns zero).
+int launch_init(const MomentsRun &run, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s);
+// One fused step.  first = 1: y = H' x (y written to zy, z not read).
+// first = 0: zy <- 2 H' x - zy.  Dot products of this step go to sums[step].
+int launch_step(const MomentsRun &run, const void *x, void *zy, int first, int step,
+                cudaStream_t s);
+// mu, mu_M, mu_M2 (device, may be NULL except mu) from sums; sets *flag on |mu| > 1+1e-6.
+int launch_assemble(const MomentsRun &run, double *mu, double *mu_M, double *mu_M2,
+                    cudaStream_t s);
+
+}  // namespace kpm

@@ -1,0 +1,385 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP64 moments |d mu_n| <= 1e-10 max(1, |mu_n|); FP32-vector
+moments |d mu_n| <= 1e-5; thermodynamics <= 1e-9 max(1, |value|);
+gradients <= 1e-9 relative against the oracle's tangent derivative and
+<= 1e-4 relative against central finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import kpm_workloads as W
+import paper_2104_13218_gb300 as kpm
+from oracle import c_oracle
+from oracle import kpm_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+def _exact_bounds(model, n_up, eps):
+    bi, bj, J = model.arrays()
+    a, b = [], []
+    for k in n_up:
+        e = O.eigenvalues(model.n_sites, bi, bj, J, k)
+        ai, bi_ = O.rescale(e.min(), e.max(), eps)
+        a.append(ai)
+        b.append(bi_)
+    return np.array(a), np.array(b)
+
+
+def _oracle_runs(model, n_up, a, b, K, R, seed, r0=0, max_steps=0):
+    bi, bj, J = model.arrays()
+    return [c_oracle.moments(model.n_sites, bi, bj, J, k, a[i], b[i], K, R, seed, r0, max_steps)
+            for i, k in enumerate(n_up)]
+
+
+def _check_moments(gpu, ref_runs, n_up, model, tol, upto=None):
+    for i, k in enumerate(n_up):
+        ref = ref_runs[i]
+        sl = slice(0, upto)
+        g = gpu["mu"][i][sl]
+        r = ref["mu"][sl]
+        err = np.abs(g - r) / np.maximum(1.0, np.abs(r))
+        assert err.max() <= tol, (k, err.max(), int(err.argmax()))
+        if k < 0:
+            for q in ("mu_M", "mu_M2"):
+                err = np.abs(gpu[q][i][sl] - ref[q][sl]) / np.maximum(1.0, np.abs(ref[q][sl]))
+                assert err.max() <= tol * 10, (q, err.max())
+        else:
+            M = k - model.n_sites / 2
+            assert np.allclose(gpu["mu_M"][i][sl], M * gpu["mu"][i][sl], rtol=0, atol=1e-14 * (1 + M * M))
+            assert np.allclose(gpu["mu_M2"][i][sl], M * M * gpu["mu"][i][sl], rtol=0, atol=1e-13 * (1 + M ** 4))
+
+
+# --------------------------------------------------------------------------- moments
+
+def test_ring10_full_space_fp64_matches_oracle():
+    w = W.workload("ring10_full")
+    a, b = _exact_bounds(w.model, range(11), w.eps)
+    e_lo = min(O.eigenvalues(10, *w.model.arrays(), k).min() for k in range(11))
+    e_hi = max(O.eigenvalues(10, *w.model.arrays(), k).max() for k in range(11))
+    a, b = O.rescale(e_lo, e_hi, w.eps)
+    gpu = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=[a], b=[b], precision="fp64")
+    ref = _oracle_runs(w.model, w.n_up, [a], [b], w.K, w.R, w.seed)
+    _check_moments(gpu, ref, w.n_up, w.model, TOL64)
+    # and the numpy oracle (independent rank and recursion) agrees as well
+    npy = O.sector_moments(w.model.arrays(), 10, -1, a, b, w.K, w.R, w.seed)
+    assert np.max(np.abs(gpu["mu"][0] - npy["mu"])) < TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_all_sectors_ragged_in_one_launch(precision, tol):
+    model = W.ring(12)
+    n_up = W.all_sectors(12)           # dims 1, 12, 66, ..., 924, ..., 1
+    a, b = _exact_bounds(model, n_up, 0.025)
+    gpu = kpm.moments(model, n_up, 64, 7, 11, a=a, b=b, precision=precision)
+    ref = _oracle_runs(model, n_up, a, b, 64, 7, 11)
+    _check_moments(gpu, ref, n_up, model, tol)
+    assert np.allclose(gpu["mu"][:, 0], 1.0, atol=1e-6 if precision == "fp32" else 1e-14)
+
+
+@pytest.mark.parametrize("precision,R", [("fp64", 1), ("fp64", 3), ("fp64", 20), ("fp64", 100),
+                                         ("fp64", 150), ("fp64", 256), ("fp32", 1), ("fp32", 4),
+                                         ("fp32", 25), ("fp32", 100), ("fp32", 260), ("fp32", 512)])
+def test_row_layouts(precision, R):
+    """Every lanes-per-state / chunks-per-lane layout, on a random model with mixed sectors."""
+    model = W.random_bonds(12, 18, 4)
+    n_up = [6, 3, -1]
+    a, b = _exact_bounds(model, [6, 3], 0.05)
+    e_all = np.concatenate([O.eigenvalues(12, *model.arrays(), k) for k in range(13)])
+    af, bf = O.rescale(e_all.min(), e_all.max(), 0.05)
+    a = np.append(a, af)
+    b = np.append(b, bf)
+    K = 16
+    gpu = kpm.moments(model, n_up, K, R, 5, a=a, b=b, r0=3, precision=precision)
+    ref = _oracle_runs(model, n_up, a, b, K, R, 5, r0=3)
+    _check_moments(gpu, ref, n_up, model, TOL64 if precision == "fp64" else TOL32)
+
+
+def test_many_tiles_and_ragged_tail():
+    """A sector spanning many tiles with a ragged last tile (N = 16, k = 7: 11440 states)."""
+    model = W.j1j2_chain(16, 1.0, 0.4)
+    n_up = [7, 8]
+    a, b = _exact_bounds(model, n_up, 0.025)
+    gpu = kpm.moments(model, n_up, 40, 6, 21, a=a, b=b, precision="fp64")
+    ref = _oracle_runs(model, n_up, a, b, 40, 6, 21)
+    _check_moments(gpu, ref, n_up, model, TOL64)
+
+
+def test_edge_cases():
+    # K = 2 (one matrix-vector product), R = 1, a one-state sector
+    model = W.ring(6)
+    a, b = _exact_bounds(model, [0, 3], 0.025)
+    gpu = kpm.moments(model, [0, 3], 2, 1, 3, a=a, b=b)
+    ref = _oracle_runs(model, [0, 3], a, b, 2, 1, 3)
+    _check_moments(gpu, ref, [0, 3], model, TOL64)
+    # a model without bonds: H = 0, mu_n = T_n(-b/a) exactly
+    empty = W.Model("empty", 5, (), (), (), ())
+    x = -0.3 / 1.7
+    out = kpm.moments(empty, [2, -1], 12, 4, 1, a=[1.7, 1.7], b=[0.3, 0.3])
+    expect = np.cos(np.arange(12) * math.acos(x))
+    assert np.max(np.abs(out["mu"] - expect[None, :])) < 1e-13
+
+
+def test_rescaling_outside_spectrum_is_flagged():
+    model = W.ring(8)
+    with pytest.raises(kpm.KPMError) as exc:
+        kpm.moments(model, [4], 40, 2, 1, a=[1.0], b=[0.0])
+    assert exc.value.code == 6
+    out = kpm.moments(model, [4], 40, 2, 1, a=[1.0], b=[0.0], allow_ebounds=True)
+    assert out["status"] == 6
+
+
+def test_deterministic_and_device_outputs_match_host():
+    model = W.ring(14)
+    n_up = W.all_sectors(14)
+    a, b = _exact_bounds(model, n_up, 0.025)
+    for prec in ("fp64", "fp32"):
+        h1 = kpm.moments(model, n_up, 100, 9, 2, a=a, b=b, precision=prec)
+        h2 = kpm.moments(model, n_up, 100, 9, 2, a=a, b=b, precision=prec)
+        assert np.array_equal(h1["mu"], h2["mu"])
+        ws = torch.empty(kpm.moments_workspace_size(model, n_up, 100, 9, prec), dtype=torch.uint8,
+                         device="cuda")
+        d = kpm.moments(model, n_up, 100, 9, 2, a=a, b=b, precision=prec, device=True, workspace=ws)
+        assert np.array_equal(d["mu"].cpu().numpy(), h1["mu"])
+        assert np.array_equal(d["mu_M2"].cpu().numpy(), h1["mu_M2"])
+
+
+def test_disjoint_vector_ranges_average_to_the_joint_run():
+    model = W.ring(10)
+    a, b = _exact_bounds(model, [5], 0.025)
+    joint = kpm.moments(model, [5], 30, 8, 9, a=a, b=b)["mu"]
+    p1 = kpm.moments(model, [5], 30, 3, 9, a=a, b=b, r0=0)["mu"]
+    p2 = kpm.moments(model, [5], 30, 5, 9, a=a, b=b, r0=3)["mu"]
+    assert np.max(np.abs((3 * p1 + 5 * p2) / 8 - joint)) < 1e-14
+
+
+# --------------------------------------------------------------------------- bounds
+
+@pytest.mark.parametrize("name,model", [("ring12", W.ring(12)), ("random", W.random_bonds(11, 16, 2)),
+                                        ("ladder", W.ladder(12))])
+def test_bounds_enclose_the_exact_spectrum(name, model):
+    n = model.n_sites
+    n_up = W.all_sectors(n) + [-1]
+    res = kpm.bounds(model, n_up, eps=0.025, max_iter=150, tol=1e-8, seed=4)
+    bi, bj, J = model.arrays()
+    for i, k in enumerate(n_up):
+        if k < 0:
+            e = np.concatenate([O.eigenvalues(n, bi, bj, J, kk) for kk in range(n + 1)])
+        else:
+            e = O.eigenvalues(n, bi, bj, J, k)
+        scale = max(1.0, abs(e).max())
+        assert res["e_min"][i] <= e.min() + 1e-9 * scale, (k, res["e_min"][i], e.min())
+        assert res["e_max"][i] >= e.max() - 1e-9 * scale, (k, res["e_max"][i], e.max())
+        assert res["e_min"][i] >= e.min() - 1e-6 * scale
+        assert res["e_max"][i] <= e.max() + 1e-6 * scale
+        m, c = O.rescale(res["e_min"][i], res["e_max"][i], 0.025)
+        assert abs(res["a"][i] - m) <= 1e-12 * max(1, m) and abs(res["b"][i] - c) <= 1e-12 * max(1, abs(c))
+
+
+# --------------------------------------------------------------------------- thermo
+
+def _thermo_case(kernel, n_quad, mirror):
+    model = W.ring(10)
+    n_up = W.nonnegative_sectors(10) if mirror else W.all_sectors(10)
+    mir = [0 if k == 5 else 1 for k in n_up] if mirror else None
+    a, b = _exact_bounds(model, n_up, 0.025)
+    runs = _oracle_runs(model, n_up, a, b, 60, 5, 13)
+    dims, mult, m1, m2 = O.sector_weights(10, n_up, mir)
+    mu = np.array([r["mu"] for r in runs])
+    muM = np.array([(k - 5) * r["mu"] for k, r in zip(n_up, runs)])
+    muM2 = np.array([(k - 5) ** 2 * r["mu"] for k, r in zip(n_up, runs)])
+    return model, n_up, mir, a, b, mu, muM, muM2
+
+
+@pytest.mark.parametrize("kernel,n_quad,mirror", [("none", 0, False), ("jackson", 0, True),
+                                                  ("jackson", 97, False), ("none", 200, True)])
+def test_thermo_matches_oracle(kernel, n_quad, mirror):
+    model, n_up, mir, a, b, mu, muM, muM2 = _thermo_case(kernel, n_quad, mirror)
+    T = W.log_grid(0.05, 10.0, 100)
+    secs = kpm.sector_set(10, n_up, a, b, mir)
+    got = kpm.thermo(mu, muM, muM2, secs, T, kernel=kernel, n_quad=n_quad)
+    runs = [{"mu": m} for m in mu]
+    ref = O.thermo_from_runs(10, n_up, runs, a, b, T, n_quad=n_quad, kernel=kernel, mirror=mir)
+    for q in ("lnZ", "E", "C", "chi"):
+        err = np.abs(got[q] - ref[q]) / np.maximum(1.0, np.abs(ref[q]))
+        assert err.max() <= 1e-9, (q, err.max())
+    assert np.array_equal(got["signZ"], ref["signZ"])
+    # device arrays give the same numbers
+    dev = kpm.thermo(torch.tensor(mu, device="cuda"), torch.tensor(muM, device="cuda"),
+                     torch.tensor(muM2, device="cuda"), secs, T, kernel=kernel, n_quad=n_quad)
+    for q in ("lnZ", "E", "C", "chi"):
+        assert np.array_equal(dev[q].cpu().numpy(), got[q])
+
+
+def test_thermo_full_space_moments_match_oracle():
+    w = W.workload("ring10_full")
+    e = np.concatenate([O.eigenvalues(10, *w.model.arrays(), k) for k in range(11)])
+    a, b = O.rescale(e.min(), e.max(), w.eps)
+    gpu = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=[a], b=[b])
+    secs = kpm.sector_set(10, w.n_up, [a], [b])
+    got = kpm.thermo(gpu["mu"], gpu["mu_M"], gpu["mu_M2"], secs, w.T, kernel=w.kernel)
+    runs = [O.sector_moments(w.model.arrays(), 10, -1, a, b, w.K, w.R, w.seed)]
+    ref = O.thermo_from_runs(10, w.n_up, runs, [a], [b], w.T, kernel=w.kernel)
+    for q in ("lnZ", "E", "C", "chi"):
+        err = np.abs(got[q] - ref[q]) / np.maximum(1.0, np.abs(ref[q]))
+        assert err.max() <= 1e-9, (q, err.max())
+
+
+def test_thermo_backward_matches_autograd_of_oracle():
+    model, n_up, mir, a, b, mu, muM, muM2 = _thermo_case("jackson", 0, True)
+    T = W.log_grid(0.1, 5.0, 50)
+    rng = np.random.default_rng(3)
+    cot = {k: rng.standard_normal(len(T)) for k in ("lnZ", "E", "C", "chi")}
+    secs = kpm.sector_set(10, n_up, a, b, mir)
+    got = kpm.thermo_backward(mu, muM, muM2, secs, T, cot, kernel="jackson")
+    tmu = [torch.tensor(m, requires_grad=True) for m in mu]
+    dims, mult, m1, m2 = O.sector_weights(10, n_up, mir)
+    out = O.thermo([t for t in tmu], [m1[i] * tmu[i] for i in range(len(tmu))],
+                   [m2[i] * tmu[i] for i in range(len(tmu))], dims, mult, a, b, T,
+                   kernel="jackson", torch_mod=torch)
+    L = sum((out[k] * torch.tensor(cot[k])).sum() for k in ("lnZ", "E", "C", "chi"))
+    L.backward()
+    # chain rule through mu_M = M mu and mu_M2 = M^2 mu
+    Ms = np.array([k - 5 for k in n_up], dtype=float)
+    total = got["mu"] + Ms[:, None] * got["mu_M"] + (Ms ** 2)[:, None] * got["mu_M2"]
+    ref = np.array([t.grad.numpy() for t in tmu])
+    scale = np.abs(ref).max()
+    assert np.abs(total - ref).max() <= 1e-9 * scale
+
+
+# --------------------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("n_up,ckpt", [([5], 4), ([4, 5, 6], 7), ([-1], 3)])
+def test_moments_backward_matches_tangent_oracle(n_up, ckpt):
+    model = W.j1j2_chain(10, 1.0, 0.35)
+    bi, bj, J = model.arrays()
+    cls = model.classes()
+    K, R, seed = 40, 3, 17
+    if n_up == [-1]:
+        e = np.concatenate([O.eigenvalues(10, bi, bj, J, k) for k in range(11)])
+        a = np.array([O.rescale(e.min(), e.max(), 0.05)[0]])
+        b = np.array([O.rescale(e.min(), e.max(), 0.05)[1]])
+    else:
+        a, b = _exact_bounds(model, n_up, 0.05)
+    rng = np.random.default_rng(7)
+    g = {k: rng.standard_normal((len(n_up), K)) for k in ("mu", "mu_M", "mu_M2")}
+    got = kpm.moments_backward(model, cls, 2, n_up, a, b, K, R, seed, g, ckpt_interval=ckpt)
+    ref = np.zeros(2)
+    for i, k in enumerate(n_up):
+        jac = O.moment_jacobian(10, bi, bj, J, cls, k, a[i], b[i], K, R, seed)
+        if k < 0:
+            st = O.sector_states(10, -1)
+            M = O.magnetisation(st, 10)
+            # weighted tangents: differentiate the weighted moments as well
+            jm = _weighted_jacobian(model, a[i], b[i], K, R, seed, M)
+            jm2 = _weighted_jacobian(model, a[i], b[i], K, R, seed, M * M)
+            ref += jac @ g["mu"][i] + jm @ g["mu_M"][i] + jm2 @ g["mu_M2"][i]
+        else:
+            Mk = k - 5
+            ref += jac @ (g["mu"][i] + Mk * g["mu_M"][i] + Mk * Mk * g["mu_M2"][i])
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.abs(ref).max(), (got, ref)
+
+
+def _weighted_jacobian(model, a, b, K, R, seed, weight):
+    """Finite-difference-free tangent of the W-weighted moments (W diagonal), for the test."""
+    bi, bj, J = model.arrays()
+    cls = model.classes()
+    st = O.sector_states(model.n_sites, -1)
+    D = len(st)
+    import scipy.sparse as sp
+    H = O.hamiltonian(model.n_sites, bi, bj, J, st)
+    Hs = (H - b * sp.identity(D, format="csr")) / a
+    v0 = O.rademacher_vectors(seed, 0, R, st)
+    Wc = weight[:, None]
+    jac = np.zeros((2, K))
+    for p in range(2):
+        Hp = O.hamiltonian(model.n_sites, bi, bj, J, st, bond_weights=(cls == p).astype(float)) / a
+        v_prev, v_cur = v0, Hs @ v0
+        d_prev, d_cur = np.zeros_like(v0), Hp @ v0
+        jac[p, 1] = np.sum(d_cur * Wc * v0) / R
+        for n in range(1, K // 2):
+            v_next = 2.0 * (Hs @ v_cur) - v_prev
+            d_next = 2.0 * (Hp @ v_cur) + 2.0 * (Hs @ d_cur) - d_prev
+            jac[p, 2 * n] = 4.0 * np.sum(d_cur * Wc * v_cur) / R
+            jac[p, 2 * n + 1] = 2.0 * (np.sum(d_next * Wc * v_cur) + np.sum(v_next * Wc * d_cur)) / R - jac[p, 1]
+            v_prev, v_cur, d_prev, d_cur = v_cur, v_next, d_cur, d_next
+    return jac
+
+
+def test_autograd_matches_finite_differences():
+    model = W.j1j2_chain(10, 1.0, 0.3)
+    n_up = W.nonnegative_sectors(10)
+    mirror = [0 if k == 5 else 1 for k in n_up]
+    a, b = _exact_bounds(model, n_up, 0.2)   # wide margin: the couplings move during FD
+    T = W.log_grid(0.3, 5.0, 20)
+    spec = dict(model=model, n_up=n_up, mirror=mirror, a=a, b=b, K=120, R=6, seed=3, T=T,
+                kernel="jackson", ckpt_interval=16)
+    theta = torch.tensor([1.0, 0.3], dtype=torch.float64, requires_grad=True)
+    target = torch.linspace(0.05, 0.2, len(T), dtype=torch.float64)
+
+    def loss(th):
+        lnZ, E, C, chi = kpm.chebyshev_thermo(th, spec)
+        return ((chi - target) ** 2).mean() + 0.1 * C.sum() + 0.01 * lnZ.sum() + 0.05 * E.sum()
+
+    L = loss(theta)
+    L.backward()
+    h = 1e-5
+    for p in range(2):
+        tp = theta.detach().clone()
+        tm = theta.detach().clone()
+        tp[p] += h
+        tm[p] -= h
+        fd = (loss(tp).item() - loss(tm).item()) / (2 * h)
+        assert abs(theta.grad[p].item() - fd) <= 1e-4 * max(abs(fd), 1e-8), (p, theta.grad[p].item(), fd)
+
+
+# --------------------------------------------------------------------------- full-size workloads
+
+def test_ring20_all_sectors_full_size_sampled():
+    """The benchmark workload (ring N=20, 21 sectors, R=100, K=1000) in both precisions:
+    the small sectors against the oracle in full, the S^z=0 sector's first moments
+    against a bounded oracle run, and mu_0 = 1, |mu_n| <= 1 everywhere."""
+    w = W.workload("ring20_sectors")
+    bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=100, tol=1e-8, seed=w.seed)
+    a, b = bnd["a"], bnd["b"]
+    small = [i for i, k in enumerate(w.n_up) if math.comb(20, k) <= 4845]
+    mid = w.n_up.index(10)
+    ref_small = _oracle_runs(w.model, [w.n_up[i] for i in small], a[small], b[small], w.K, w.R, w.seed)
+    ref_mid = _oracle_runs(w.model, [10], a[[mid]], b[[mid]], w.K, w.R, w.seed, max_steps=4)[0]
+    for prec, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        gpu = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=a, b=b, precision=prec)
+        for j, i in enumerate(small):
+            err = np.abs(gpu["mu"][i] - ref_small[j]["mu"]).max()
+            assert err <= tol, (prec, w.n_up[i], err)
+        err = np.abs(gpu["mu"][mid][:8] - ref_mid["mu"][:8]).max()
+        assert err <= tol, (prec, err)
+        assert np.abs(gpu["mu"][:, 0] - 1).max() <= (1e-6 if prec == "fp32" else 1e-13)
+        assert np.abs(gpu["mu"]).max() <= 1 + 1e-6
+
+
+def test_j1j2_square_full_space_full_size_properties():
+    """The 4x6 J1-J2 torus over the full 2^24 space, R=64: the FP32-vector run at K=2000
+    obeys mu_0 = 1, mu^M_0 = 0, mu^M2_0 = N/4 and |mu_n| <= 1, and at K=200 it agrees
+    with the FP64 run to 1e-5 (FP64 at K=2000 is left to the benchmark: it is
+    arithmetic-bound on this GPU)."""
+    w = W.workload("j1j2sq24_full")
+    bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=100, tol=1e-8, seed=w.seed)
+    r32 = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=bnd["a"], b=bnd["b"], precision="fp32")
+    assert abs(r32["mu"][0, 0] - 1) < 1e-6
+    assert abs(r32["mu_M"][0, 0]) < 1e-6
+    assert abs(r32["mu_M2"][0, 0] - 6.0) < 1e-5
+    assert np.abs(r32["mu"]).max() <= 1 + 1e-6
+    s64 = kpm.moments(w.model, w.n_up, 200, w.R, w.seed, a=bnd["a"], b=bnd["b"], precision="fp64")
+    s32 = kpm.moments(w.model, w.n_up, 200, w.R, w.seed, a=bnd["a"], b=bnd["b"], precision="fp32")
+    assert abs(s64["mu"][0, 0] - 1) < 1e-13
+    assert abs(s64["mu_M"][0, 0]) < 1e-13
+    assert abs(s64["mu_M2"][0, 0] - 6.0) < 1e-12
+    assert np.abs(s32["mu"] - s64["mu"]).max() <= TOL32
+    assert np.abs(s32["mu"] - r32["mu"][:, :200]).max() == 0.0
