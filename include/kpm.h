@@ -69,7 +69,9 @@ extern "C" {
 
 /* vector storage precision of the moment loop */
 #define KPM_FP64 0      /* vectors and arithmetic in FP64 */
-#define KPM_FP32 1      /* vectors and arithmetic in FP32, dot products reduced in FP64 */
+#define KPM_FP32 1      /* vectors and arithmetic in FP32, dot products reduced in FP64;
+                           sectors below 1024 states are stored in FP64 (in such tiny
+                           sectors FP32 rounding stays coherent and grows with the order) */
 
 /* damping kernel g_n (Eq. E-2-8) */
 #define KPM_KERNEL_NONE 0     /* g_n = 1 */
@@ -201,8 +203,8 @@ int kpm_thermo_backward(int32_t n_sectors, int32_t n_moments, const double *mu,
  * (v_n, v_{n+1}) every ckpt_interval steps (0 -> 32), then sweeps back with
  * lambda_n = d_n + 2 H' lambda_{n+1} - lambda_{n+2}, regenerating v_{n-1} =
  * 2 H' v_n - v_{n+1} on the way and resetting it to the stored pair at each
- * checkpoint, and accumulates dL/dJ_b = sum_n (2/a) <lambda_{n+1}, H_b v_n>
- * + (1/a) <lambda_1, H_b v_0>.  FP64 only (precision must be KPM_FP64).
+ * checkpoint, and accumulates dL/dJ_b = (1/R) [sum_n (2/a) <lambda_{n+1}, H_b v_n>
+ * + (1/a) <lambda_1, H_b v_0>] (dot products over all R vectors).  FP64 only (precision must be KPM_FP64).
  * Workspace: kpm_moments_backward_workspace_size.
  */
 int kpm_moments_backward(const kpm_model *model, const int32_t *bond_class, int32_t n_classes,

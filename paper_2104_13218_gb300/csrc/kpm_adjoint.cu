@@ -12,7 +12,8 @@
 //   d_n = 4 w_{2n} v_n + 2 w_{2n+1} v_{n+1} + c_n v_{n-1},
 //   c_n = 2 w_{2n-1} for n >= 2,  c_1 = w_1 - sum_{j>=1} w_{2j+1}
 // (w_i = 0 for i >= K), and with a, b fixed and H_b = S_i . S_j,
-//   dL/dJ_b = sum_{n=1}^{S-1} (2/a) <lambda_{n+1}, H_b v_n> + (1/a) <lambda_1, H_b v_0>.
+//   dL/dJ_b = (1/R) [sum_{n=1}^{S-1} (2/a) <lambda_{n+1}, H_b v_n> + (1/a) <lambda_1, H_b v_0>]
+// (the dot products run over all R vectors; 1/R is the average in mu_n).
 // The reverse sweep regenerates v_{n-1} = 2 H' v_n - v_{n+1} in the same pass
 // that builds lambda_n (both gather the same bit-flipped neighbours) and
 // resets the pair (v_{n-1}, v_n) from the copies stored every ckpt_interval
@@ -203,13 +204,16 @@ __global__ void adjoint_hbar_kernel(const double *g0, const double *g1, const do
   hbar[i] = h;
 }
 
-// dL/dtheta_p = sum over tiles (tile order) of gpart[t][p]
-__global__ void adjoint_final_kernel(const double *gpart, int n_tiles, int P, double *out) {
+// dL/dtheta_p = (1/R) sum over tiles (tile order) of gpart[t][p]; the 1/R is the
+// average over the random vectors in mu_n = (1/R) sum_r <r|T_n|r>, left out of
+// the per-vector recursion above.
+__global__ void adjoint_final_kernel(const double *gpart, int n_tiles, int P, double inv_R,
+                                     double *out) {
   const int p = blockIdx.x;
   double v = 0.0;
   for (int t = threadIdx.x; t < n_tiles; t += 32) v += gpart[(int64_t)t * kMaxClasses + p];
   v = warp_sum(v);
-  if (threadIdx.x == 0) out[p] = v;
+  if (threadIdx.x == 0) out[p] = v * inv_R;
 }
 
 namespace {
@@ -426,7 +430,7 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
   // n = 0: (1/a) <lambda_1, H_b v_0> with Vg = v_0, Lg = lambda_1
   KPM_TRY(launch(2, 0, Vg, Vo, Lg, Lo, 1, 0));
   adjoint_final_kernel<<<ap.n_classes, 32, 0, stream>>>(gpart, (int)run.plan.tiles.size(),
-                                                        ap.n_classes, dtheta);
+                                                        ap.n_classes, 1.0 / R, dtheta);
   KPM_CUDA(cudaGetLastError());
   count_launches(1);
   if (on_device)

@@ -209,7 +209,8 @@ int prepare_bounds(const kpm_model *m, int n_sectors, const int32_t *n_up, Bound
   bl->bytes = 2 * r.vec_bytes + tables_bytes(r.plan) +
               align256(std::max<size_t>(1, r.plan.tiles.size()) * 2 * sizeof(double)) +
               2 * align256((size_t)(kMaxLanczos + 1) * n_sectors * 2 * sizeof(double)) +
-              align256((size_t)4 * (kMaxLanczos + 1) * sizeof(int)) + 1024;
+              align256((size_t)4 * (kMaxLanczos + 2) * sizeof(int)) +
+              align256((size_t)n_sectors * 2 * sizeof(double)) + 1024;
   return KPM_OK;
 }
 
@@ -248,8 +249,9 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   const size_t nab = (size_t)(kMaxLanczos + 1) * n_sectors * 2;
   double *alpha = arena.take<double>(nab);
   double *beta = arena.take<double>(nab);
-  int *counters = arena.take<int>((size_t)4 * (kMaxLanczos + 1));
-  KPM_REQUIRE(P && Q && partials && alpha && beta && counters, KPM_ENOMEM,
+  int *counters = arena.take<int>((size_t)4 * (kMaxLanczos + 2));
+  double *norm0 = arena.take<double>((size_t)n_sectors * 2);
+  KPM_REQUIRE(P && Q && partials && alpha && beta && counters && norm0, KPM_ENOMEM,
               "workspace too small for kpm_bounds");
   std::vector<SectorDev> sec(n_sectors);
   for (int i = 0; i < n_sectors; ++i) {
@@ -262,12 +264,14 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
     sec[i].Mval = 0.0;
   }
   KPM_TRY(upload_tables(r.plan, sec, arena, stream, &r.tb));
-  KPM_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4 * (kMaxLanczos + 1), stream));
+  KPM_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4 * (kMaxLanczos + 2), stream));
   KPM_CUDA(cudaMemsetAsync(beta, 0, sizeof(double) * nab, stream));
   KPM_CUDA(cudaMemsetAsync(alpha, 0, sizeof(double) * nab, stream));
-  KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));
-  // q_0: normalised random signs, two sequences per sector
-  KPM_TRY(launch_init(r, Q, seed, 0, stream));
+  // q_0: uniform random values (a vector of +-1 signs can be exactly orthogonal
+  // to an eigenvector in a small sector), two sequences per sector, normalised
+  // below by the kernels' own |w| / scale passes (modes 2 and 3 with alpha = 0).
+  KPM_TRY(launch_init(r, P, seed, 0, stream, true));
+  KPM_CUDA(cudaMemsetAsync(Q, 0, r.vec_bytes, stream));
 
   double jabs = 0.0;
   for (int b = 0; b < model->n_bonds; ++b) jabs += std::fabs(model->J[b]);
@@ -278,6 +282,22 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   LanczosArgs la;
   la.tb = r.tb;
   la.partials = partials;
+  la.breakdown = 0.0;
+  // normalise the start vectors: norm0 = |P| (mode 2 with zero alpha), P /= norm0 (mode 3)
+  for (int mode = 2; mode <= 3; ++mode) {
+    la.P = P;
+    la.Q = Q;
+    la.mode = mode;
+    la.queue = counters + 4 * (kMaxLanczos + 1) + (mode == 2 ? 0 : 2);
+    la.done = la.queue + 1;
+    la.coef = mode == 2 ? beta : norm0;  // beta[0 .. n_sectors*2) is zero here
+    la.out = norm0;
+    void *args[] = {(void *)&la, (void *)&r.bonds};
+    KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
+    count_launches(1);
+  }
+  std::swap(P, Q);  // Q = q_0
+  KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));  // q_{-1} = 0
   la.breakdown = 1e-12 * std::max(1.0, jabs);
   for (int j = 0; j < max_iter; ++j) {
     for (int mode = 1; mode <= 3; ++mode) {

@@ -70,6 +70,8 @@ struct SectorDev {
   double inv_a;      // 1/a
   double b;          // shift
   double Mval;       // magnetisation of the sector (full space: 0)
+  int32_t out_index; // row of this sector in the caller's moment arrays
+  int32_t pad2;
 };
 
 // The S^z basis of one call: split rank tables shared by all sectors.
@@ -120,14 +122,34 @@ struct TablesDev {
   int32_t pad;
 };
 
+constexpr int kMaxGroups = 4;       // distinct coupling values handled by the grouped step
+constexpr int kMaxDiagTable = 4096; // entries of the per-sector diagonal table
+
 // Bond list as kernel parameter (constant bank, broadcast to the warp).
+// Bonds with equal J form a group; `order` lists the bonds group by group.
+// The step kernel sums the gathered neighbours of each group and applies the
+// group's coupling once, and reads the diagonal from a table indexed by the
+// number of anti-aligned bonds per group, index = sum_g n_g * tstride[g].
 struct BondsDev {
   int32_t n_bonds;
   int32_t n_sites;
   double J_quarter_sum;            // sum_b J_b / 4
   uint64_t mask[kMaxBonds];        // (1 << i_b) | (1 << j_b)
   double J[kMaxBonds];
+  int32_t n_groups;                // 0: more than kMaxGroups values (per-bond path)
+  int32_t table_size;              // prod_g (group size + 1)
+  int32_t gstart[kMaxGroups + 1];  // group g = order[gstart[g] .. gstart[g+1])
+  int32_t tstride[kMaxGroups];
+  double gJ[kMaxGroups];
+  uint8_t order[kMaxBonds];
+  // Cooperative layouts (G >= 2 lanes per state): in pass p lane j of a group
+  // tests bond p*G + j; pmask[p][g] has bit j set when that bond is in group g.
+  int32_t G;                       // lanes per state this table was built for
+  int32_t n_pass;                  // ceil(n_bonds / G)
+  uint32_t pmask[kMaxBonds / 2][kMaxGroups];
 };
+// Fills pmask / n_pass for a layout with G lanes per state.
+void fill_pass_masks(BondsDev *b, int G);
 void fill_bonds(const kpm_model *m, BondsDev *out);
 
 // Simple bump allocator over a workspace region (256-byte aligned pieces).

@@ -43,11 +43,22 @@ __global__ void __launch_bounds__(kThreads)
   using V = typename C::type;
   constexpr int W = C::W;
   constexpr int NQ = FULL ? 6 : 2;
-  __shared__ T s_aj[kMaxBonds];
-  __shared__ T s_jh[kMaxBonds];
+  // The FP32 form carries every coefficient of H' as an unevaluated sum hi + lo
+  // of two floats: rounding the operator itself to FP32 would perturb it the
+  // same way at every step and shift its spectrum; with the pair, the
+  // remaining FP32 rounding (of the vectors and the sums) changes from step
+  // to step.
+  constexpr bool PAIR = sizeof(T) == 4;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  T *s_dh = reinterpret_cast<T *>(s_dyn);  // diagonal A (d - b), hi part, [table_size]
+  T *s_dl = s_dh + bd.table_size;          // lo part (FP32 only)
+  __shared__ T s_aj[kMaxBonds];            // per-bond path: A J_b / 2
+  __shared__ T s_jh[kMaxBonds];            // per-bond path: J_b / 2
+  __shared__ T s_gh[kMaxGroups], s_gl[kMaxGroups];  // grouped path: A J_g / 2 = hi + lo
   __shared__ double s_red[kWarps * NQ];
   __shared__ int s_tile;
   __shared__ int s_last;
+  __shared__ int s_sec;
 
   const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
   V *__restrict__ zy = reinterpret_cast<V *>(a.zy);
@@ -56,7 +67,9 @@ __global__ void __launch_bounds__(kThreads)
   const bool active = grp < a.gpw;
   const int64_t crow = a.Rp / W;  // chunks per row
   const int nb = bd.n_bonds;
+  const bool grouped = bd.n_groups > 0;
   for (int b = threadIdx.x; b < nb; b += kThreads) s_jh[b] = (T)(0.5 * bd.J[b]);
+  if (threadIdx.x == 0) s_sec = -1;
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
@@ -66,7 +79,34 @@ __global__ void __launch_bounds__(kThreads)
     const Tile tile = a.tb.tiles[t];
     const SectorDev sd = a.tb.sectors[tile.sector];
     const double A = (a.first ? 1.0 : 2.0) * sd.inv_a;
-    for (int b = threadIdx.x; b < nb; b += kThreads) s_aj[b] = (T)(A * 0.5 * bd.J[b]);
+    if (s_sec != tile.sector) {
+      // coefficients of this sector's H' (rebuilt only when the sector changes)
+      __syncthreads();
+      if (grouped) {
+        if (threadIdx.x < bd.n_groups) {
+          const double c = A * 0.5 * bd.gJ[threadIdx.x];
+          const T hi = (T)c;
+          s_gh[threadIdx.x] = hi;
+          s_gl[threadIdx.x] = PAIR ? (T)(c - (double)hi) : (T)0;
+        }
+        for (int idx = threadIdx.x; idx < bd.table_size; idx += kThreads) {
+          double d = bd.J_quarter_sum;
+          for (int g = 0; g < bd.n_groups; ++g) {
+            const int size = bd.gstart[g + 1] - bd.gstart[g];
+            const int ng = (idx / bd.tstride[g]) % (size + 1);
+            d -= ng * (0.5 * bd.gJ[g]);
+          }
+          const double ad = A * (d - sd.b);
+          const T hi = (T)ad;
+          s_dh[idx] = hi;
+          if (PAIR) s_dl[idx] = (T)(ad - (double)hi);
+        }
+      } else {
+        for (int b = threadIdx.x; b < nb; b += kThreads) s_aj[b] = (T)(A * 0.5 * bd.J[b]);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_sec = tile.sector;
+    }
     __syncthreads();
 
     double acc64[NQ];
@@ -77,71 +117,231 @@ __global__ void __launch_bounds__(kThreads)
     // FULL only adds the M-weighted dot products; each tile decides its own basis
     const bool full_tile = sd.n_up < 0;
     uint32_t hb = tile.b_first;
-    if (active) {
-      for (uint32_t u = warp * a.gpw + grp; u < tile.count; u += kWarps * a.gpw) {
-        const int64_t row = tile.row0 + u;
-        uint64_t s;
+    const int G = a.G;
+    const bool coop = G >= 2;
+    const int gbase = grp * G;  // first lane of this lane's group (idle lanes: past the groups)
+    const uint32_t gmaskG = G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
+    // Warp-uniform loop over the warp's states, so that ballots and shuffles see all lanes.
+    for (uint32_t ub = warp * a.gpw; ub < tile.count; ub += kWarps * a.gpw) {
+      const uint32_t u = ub + grp;
+      const bool valid = active && u < tile.count;
+      uint64_t s = 0;
+      int64_t row = 0;
+      if (valid) {
+        row = tile.row0 + u;
         if (full_tile)
           s = (uint64_t)(row - sd.row0);
         else
           s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
-        T d = (T)bd.J_quarter_sum;
-        V acc[CPL];
+      }
+      V acc[CPL];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] = V{};
-        for (int b0 = 0; b0 < nb; b0 += 8) {
-          int64_t nrow[8];
-          bool fl[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int b = b0 + j;
-            fl[j] = false;
-            nrow[j] = 0;
-            if (b < nb) {
-              const uint64_t m = bd.mask[b];
-              const uint64_t tt = s & m;
-              if (tt != 0 && tt != m) {
-                fl[j] = true;
-                d -= s_jh[b];
-                const uint64_t f = s ^ m;
-                nrow[j] = sd.row0 + (full_tile ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
-              }
+      for (int c = 0; c < CPL; ++c) acc[c] = V{};
+      T ad_hi = 0, ad_lo = 0;
+      if (coop) {
+        // The G lanes of a group share the state: in pass p lane `sub` tests bond
+        // p*G + sub; the ranks of the anti-aligned bonds' neighbours are then
+        // shuffled to every lane of the group, each of which gathers its chunks.
+        int tidx = 0;
+        T dsum = 0;
+        for (int p = 0; p < bd.n_pass; ++p) {
+          const int b = p * G + sub;
+          bool fl = false;
+          uint32_t nr = 0;
+          if (valid && b < nb) {
+            const uint64_t m = bd.mask[b];
+            const uint64_t tt = s & m;
+            if (tt != 0 && tt != m) {
+              fl = true;
+              const uint64_t f = s ^ m;
+              nr = full_tile ? (uint32_t)f : sector_rank(f, a.tb);
             }
           }
+          const uint32_t F =
+              (uint32_t)(((uint64_t)__ballot_sync(0xffffffffu, fl) >> gbase) & gmaskG);
+          if (grouped) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (fl[j]) {
-              const T aj = s_aj[b0 + j];
-              const V *src = x + nrow[j] * crow + sub;
+            for (int g = 0; g < kMaxGroups; ++g) {
+              if (g < bd.n_groups) {
+                uint32_t Fg = F & bd.pmask[p][g];
+                tidx += __popc(Fg) * bd.tstride[g];
+                const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(Fg));
+                V gs[CPL];
 #pragma unroll
-              for (int c = 0; c < CPL; ++c) {
-                const V v = __ldg(src + c * a.G);
+                for (int c = 0; c < CPL; ++c) gs[c] = V{};
+                for (int i = 0; i < nmax; ++i) {
+                  const int j = Fg ? __ffs(Fg) - 1 : 0;
+                  const uint32_t rk = __shfl_sync(0xffffffffu, nr, (gbase + j) & 31);
+                  if (Fg) {
+                    Fg &= Fg - 1;
+                    const V *src = x + (sd.row0 + (int64_t)rk) * crow + sub;
 #pragma unroll
-                for (int e = 0; e < W; ++e)
-                  C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
+                    for (int c = 0; c < CPL; ++c) {
+                      const V v = __ldg(src + c * G);
+#pragma unroll
+                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v, e));
+                    }
+                  }
+                }
+                const T gh = s_gh[g], gl = s_gl[g];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+                  for (int e = 0; e < W; ++e) {
+                    T v = fma(gh, C::get(gs[c], e), C::get(acc[c], e));
+                    if (PAIR) v = fma(gl, C::get(gs[c], e), v);
+                    C::set(acc[c], e, v);
+                  }
+                }
+              }
+            }
+          } else {
+            uint32_t Fb = F;
+            const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(Fb));
+            for (int i = 0; i < nmax; ++i) {
+              const int j = Fb ? __ffs(Fb) - 1 : 0;
+              const uint32_t rk = __shfl_sync(0xffffffffu, nr, (gbase + j) & 31);
+              if (Fb) {
+                Fb &= Fb - 1;
+                const int bb = p * G + j;
+                const T aj = s_aj[bb];
+                dsum += s_jh[bb];
+                const V *src = x + (sd.row0 + (int64_t)rk) * crow + sub;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  const V v = __ldg(src + c * G);
+#pragma unroll
+                  for (int e = 0; e < W; ++e)
+                    C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
+                }
               }
             }
           }
         }
-        const T ad = A_t * (d - b_t);
+        if (grouped) {
+          ad_hi = s_dh[tidx];
+          if (PAIR) ad_lo = s_dl[tidx];
+        } else {
+          ad_hi = A_t * (((T)bd.J_quarter_sum - dsum) - b_t);
+        }
+      } else if (valid) {
+        // one lane per state: the lane walks all bonds itself
+        if (grouped) {
+          int tidx = 0;
+#pragma unroll
+          for (int g = 0; g < kMaxGroups; ++g) {
+            if (g < bd.n_groups) {
+              V gs[CPL];
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) gs[c] = V{};
+              int cnt = 0;
+              const int k1 = bd.gstart[g + 1];
+              for (int k0 = bd.gstart[g]; k0 < k1; k0 += 8) {
+                int64_t nrow[8];
+                bool fl[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  fl[j] = false;
+                  nrow[j] = 0;
+                  if (k0 + j < k1) {
+                    const uint64_t m = bd.mask[bd.order[k0 + j]];
+                    const uint64_t tt = s & m;
+                    if (tt != 0 && tt != m) {
+                      fl[j] = true;
+                      const uint64_t f = s ^ m;
+                      nrow[j] = sd.row0 + (full_tile ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+                    }
+                  }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  if (fl[j]) {
+                    ++cnt;
+                    const V *src = x + nrow[j] * crow + sub;
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                      const V v = __ldg(src + c * G);
+#pragma unroll
+                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v, e));
+                    }
+                  }
+                }
+              }
+              tidx += cnt * bd.tstride[g];
+              const T gh = s_gh[g], gl = s_gl[g];
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                  T v = fma(gh, C::get(gs[c], e), C::get(acc[c], e));
+                  if (PAIR) v = fma(gl, C::get(gs[c], e), v);
+                  C::set(acc[c], e, v);
+                }
+              }
+            }
+          }
+          ad_hi = s_dh[tidx];
+          if (PAIR) ad_lo = s_dl[tidx];
+        } else {
+          T d = (T)bd.J_quarter_sum;
+          for (int b0 = 0; b0 < nb; b0 += 8) {
+            int64_t nrow[8];
+            bool fl[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int b = b0 + j;
+              fl[j] = false;
+              nrow[j] = 0;
+              if (b < nb) {
+                const uint64_t m = bd.mask[b];
+                const uint64_t tt = s & m;
+                if (tt != 0 && tt != m) {
+                  fl[j] = true;
+                  d -= s_jh[b];
+                  const uint64_t f = s ^ m;
+                  nrow[j] = sd.row0 + (full_tile ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+                }
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (fl[j]) {
+                const T aj = s_aj[b0 + j];
+                const V *src = x + nrow[j] * crow + sub;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  const V v = __ldg(src + c * G);
+#pragma unroll
+                  for (int e = 0; e < W; ++e)
+                    C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
+                }
+              }
+            }
+          }
+          ad_hi = A_t * (d - b_t);
+        }
+      }
+      if (valid) {
         const V *xo = x + row * crow + sub;
         V *zo = zy + row * crow + sub;
         T pxx = 0, pyx = 0;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          const V xv = xo[c * a.G];
+          const V xv = xo[c * G];
           V zv = V{};
-          if (!a.first) zv = __ldcs(zo + c * a.G);
+          if (!a.first) zv = __ldcs(zo + c * G);
           V y;
 #pragma unroll
           for (int e = 0; e < W; ++e) {
             const T xe = C::get(xv, e);
-            const T ye = fma(ad, xe, C::get(acc[c], e)) - C::get(zv, e);
+            T h = C::get(acc[c], e);
+            if (PAIR) h = fma(ad_lo, xe, h);
+            const T ye = fma(ad_hi, xe, h) - C::get(zv, e);
             C::set(y, e, ye);
             pxx = fma(xe, xe, pxx);
             pyx = fma(ye, xe, pyx);
           }
-          zo[c * a.G] = y;
+          __stcs(zo + c * G, y);
         }
         if constexpr (sizeof(T) == 8) {
           acc64[0] += pxx;
@@ -210,6 +410,7 @@ struct InitArgs {
   TablesDev tb;
   uint64_t seed, r0;
   int R, Rp, G, gpw;
+  int uniform;  // 0: +-1/sqrt(D) signs; 1: uniform values in (-1, 1), not normalised
 };
 
 template <typename T>
@@ -244,7 +445,13 @@ __global__ void __launch_bounds__(kThreads) init_vectors_kernel(const __grid_con
         for (int e = 0; e < W; ++e) {
           const int col = ch * W + e;
           T x = 0;
-          if (col < a.R) x = (splitmix64(s_hr[col] ^ s) >> 63) ? -norm : norm;
+          if (col < a.R) {
+            const uint64_t h = splitmix64(s_hr[col] ^ s);
+            if (a.uniform)
+              x = (T)(2.0 * (((double)(h >> 11) + 0.5) * 0x1.0p-53) - 1.0);
+            else
+              x = (h >> 63) ? -norm : norm;
+          }
           C::set(val, e, x);
         }
         v[row * crow + ch] = val;
@@ -294,7 +501,7 @@ __global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) {
         const double M = a.sectors[sec].Mval;
         val = (q == 1 ? M : M * M) * m0;
       }
-      out[(int64_t)sec * a.K + n] = val;
+      out[(int64_t)a.sectors[sec].out_index * a.K + n] = val;
       if (q == 0 && !(fabs(val) <= 1.0 + 1e-6)) atomicOr(a.flag, 1);
     }
     (void)nq_out;
@@ -329,6 +536,11 @@ void *pick_step(int precision, int cpl, bool full) {
   }
 }
 
+size_t step_smem(const MomentsRun &r) {
+  // diagonal table: hi + lo floats (FP32) or one double (FP64) per entry
+  return (size_t)r.bonds.table_size * 8;
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -360,6 +572,7 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   KPM_TRY(build_plan(m, n_sectors, n_up, choose_tile_states(run->lay.gpw, rows), &run->plan));
   run->NQ = run->plan.any_full ? 6 : 2;
   fill_bonds(m, &run->bonds);
+  fill_pass_masks(&run->bonds, run->lay.G);
   run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);
   (void)full;
   return KPM_OK;
@@ -372,7 +585,8 @@ size_t run_bytes(const MomentsRun &r) {
          align256((size_t)2 * r.S * sizeof(int)) + 256;
 }
 
-int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cudaStream_t s) {
+int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cudaStream_t s,
+              const int *out_index) {
   r.vA = arena.take<char>(r.vec_bytes);
   r.vB = arena.take<char>(r.vec_bytes);
   r.partials = arena.take<double>(std::max<size_t>(1, r.plan.tiles.size() * r.NQ));
@@ -392,21 +606,25 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     sec[i].inv_a = 1.0 / a[i];
     sec[i].b = b[i];
     sec[i].Mval = r.plan.n_up[i] < 0 ? 0.0 : r.plan.n_up[i] - 0.5 * r.plan.N;
+    sec[i].out_index = out_index ? out_index[i] : i;
+    sec[i].pad2 = 0;
   }
   KPM_TRY(upload_tables(r.plan, sec, arena, s, &r.tb));
   KPM_CUDA(cudaMemsetAsync(r.counters, 0, sizeof(int) * 2 * r.S, s));
   KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
   void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
   int per_sm = 0;
-  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, step_smem(r)));
   per_sm = std::max(per_sm, 1);
   r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), (int64_t)r.plan.tiles.size());
   r.grid = std::max(r.grid, 1);
   return KPM_OK;
 }
 
-int launch_init(const MomentsRun &r, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s) {
+int launch_init(const MomentsRun &r, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s,
+                bool uniform) {
   InitArgs a;
+  a.uniform = uniform ? 1 : 0;
   a.v0 = v0;
   a.tb = r.tb;
   a.seed = seed;
@@ -442,13 +660,13 @@ int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int ste
   void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
   void *args[] = {(void *)&a, (void *)&r.bonds};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const bool prof = profiling();
+  const bool prof = r.profile && profiling();
   if (prof) {
     KPM_CUDA(cudaEventCreate(&e0));
     KPM_CUDA(cudaEventCreate(&e1));
     KPM_CUDA(cudaEventRecord(e0, s));
   }
-  KPM_CUDA(cudaLaunchKernel(fn, dim3(r.grid), dim3(kThreads), args, 0, s));
+  KPM_CUDA(cudaLaunchKernel(fn, dim3(r.grid), dim3(kThreads), args, step_smem(r), s));
   count_launches(1);
   if (prof) {
     KPM_CUDA(cudaEventRecord(e1, s));
@@ -476,6 +694,70 @@ int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2
   return KPM_OK;
 }
 
+int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
+                int precision, MomentsJob *job) {
+  KPM_TRY(validate_model(m));
+  KPM_TRY(validate_sectors(m, n_sectors, n_up));
+  job->n_sectors = n_sectors;
+  job->K = K;
+  job->nup_main.clear();
+  job->nup_side.clear();
+  job->map_main.clear();
+  job->map_side.clear();
+  for (int i = 0; i < n_sectors; ++i) {
+    const bool small = precision == KPM_FP32 && kpm_sector_dim(m->n_sites, n_up[i]) < kFP32MinSectorDim;
+    (small ? job->nup_side : job->nup_main).push_back(n_up[i]);
+    (small ? job->map_side : job->map_main).push_back(i);
+  }
+  job->has_main = !job->nup_main.empty();
+  job->has_side = !job->nup_side.empty();
+  if (job->has_main)
+    KPM_TRY(prepare_run(m, (int)job->nup_main.size(), job->nup_main.data(), K, R, precision, &job->main));
+  if (job->has_side) {
+    KPM_TRY(prepare_run(m, (int)job->nup_side.size(), job->nup_side.data(), K, R, KPM_FP64, &job->side));
+    job->side.profile = false;
+  }
+  return KPM_OK;
+}
+
+size_t job_bytes(const MomentsJob &job) {
+  return (job.has_main ? run_bytes(job.main) : 0) + (job.has_side ? run_bytes(job.side) : 0);
+}
+
+int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, cudaStream_t s) {
+  for (int part = 0; part < 2; ++part) {
+    const bool has = part == 0 ? job.has_main : job.has_side;
+    if (!has) continue;
+    MomentsRun &r = part == 0 ? job.main : job.side;
+    const std::vector<int> &map = part == 0 ? job.map_main : job.map_side;
+    std::vector<double> as(map.size()), bs(map.size());
+    for (size_t i = 0; i < map.size(); ++i) {
+      as[i] = a[map[i]];
+      bs[i] = b[map[i]];
+    }
+    KPM_TRY(setup_run(r, as.data(), bs.data(), arena, s, map.data()));
+  }
+  return KPM_OK;
+}
+
+int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
+            cudaStream_t s) {
+  for (int part = 0; part < 2; ++part) {
+    const bool has = part == 0 ? job.has_main : job.has_side;
+    if (!has) continue;
+    MomentsRun &r = part == 0 ? job.main : job.side;
+    KPM_TRY(launch_init(r, r.vA, seed, r0, s));
+    KPM_TRY(launch_step(r, r.vA, r.vB, 1, 0, s));
+    void *x = r.vB, *zy = r.vA;
+    for (int step = 1; step < r.S; ++step) {
+      KPM_TRY(launch_step(r, x, zy, 0, step, s));
+      std::swap(x, zy);
+    }
+    KPM_TRY(launch_assemble(r, mu, mu_M, mu_M2, s));
+  }
+  return KPM_OK;
+}
+
 }  // namespace kpm
 
 using namespace kpm;
@@ -483,9 +765,9 @@ using namespace kpm;
 extern "C" size_t kpm_moments_workspace_size(const kpm_model *model, int32_t n_sectors,
                                              const int32_t *n_up, int32_t n_moments, int32_t R,
                                              int32_t precision) {
-  MomentsRun run;
-  if (prepare_run(model, n_sectors, n_up, n_moments, R, precision, &run) != KPM_OK) return 0;
-  return run_bytes(run);
+  MomentsJob job;
+  if (prepare_job(model, n_sectors, n_up, n_moments, R, precision, &job) != KPM_OK) return 0;
+  return job_bytes(job);
 }
 
 extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
@@ -496,8 +778,8 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
   clear_error();
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
   KPM_REQUIRE(mu != nullptr, KPM_EINVAL, "mu is NULL");
-  MomentsRun run;
-  KPM_TRY(prepare_run(model, n_sectors, n_up, n_moments, R, precision, &run));
+  MomentsJob job;
+  KPM_TRY(prepare_job(model, n_sectors, n_up, n_moments, R, precision, &job));
   std::vector<double> av, bv;
   if (a == nullptr || b == nullptr) {
     av.resize(n_sectors);
@@ -509,11 +791,11 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
     b = bv.data();
   }
   const size_t out_bytes = align256((size_t)n_sectors * n_moments * sizeof(double));
-  const size_t need = run_bytes(run) + (on_device ? 0 : 3 * out_bytes);
+  const size_t need = job_bytes(job) + (on_device ? 0 : 3 * out_bytes);
   Workspace ws;
   KPM_TRY(ws.acquire(workspace, ws_bytes, need, stream));
   Arena arena{reinterpret_cast<char *>(ws.ptr), ws.size, 0};
-  KPM_TRY(setup_run(run, a, b, arena, stream));
+  KPM_TRY(setup_job(job, a, b, arena, stream));
   double *dmu = mu, *dmuM = mu_M, *dmuM2 = mu_M2;
   if (!on_device) {
     dmu = arena.take<double>((size_t)n_sectors * n_moments);
@@ -521,24 +803,20 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
     dmuM2 = mu_M2 ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
     KPM_REQUIRE(dmu && (!mu_M || dmuM) && (!mu_M2 || dmuM2), KPM_ENOMEM, "workspace too small");
   }
-  KPM_TRY(launch_init(run, run.vA, seed, r0, stream));
-  KPM_TRY(launch_step(run, run.vA, run.vB, 1, 0, stream));
-  void *x = run.vB, *zy = run.vA;
-  for (int step = 1; step < run.S; ++step) {
-    KPM_TRY(launch_step(run, x, zy, 0, step, stream));
-    std::swap(x, zy);
-  }
-  KPM_TRY(launch_assemble(run, dmu, dmuM, dmuM2, stream));
+  KPM_TRY(run_job(job, seed, r0, dmu, dmuM, dmuM2, stream));
   const size_t nbytes = (size_t)n_sectors * n_moments * sizeof(double);
   if (!on_device) {
     KPM_CUDA(cudaMemcpyAsync(mu, dmu, nbytes, cudaMemcpyDeviceToHost, stream));
     if (mu_M) KPM_CUDA(cudaMemcpyAsync(mu_M, dmuM, nbytes, cudaMemcpyDeviceToHost, stream));
     if (mu_M2) KPM_CUDA(cudaMemcpyAsync(mu_M2, dmuM2, nbytes, cudaMemcpyDeviceToHost, stream));
   }
-  int flag = 0;
-  KPM_CUDA(cudaMemcpyAsync(&flag, run.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  int flags[2] = {0, 0};
+  if (job.has_main)
+    KPM_CUDA(cudaMemcpyAsync(&flags[0], job.main.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  if (job.has_side)
+    KPM_CUDA(cudaMemcpyAsync(&flags[1], job.side.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
   KPM_CUDA(cudaStreamSynchronize(stream));
-  if (flag) {
+  if (flags[0] || flags[1]) {
     set_error("some |mu_n| > 1 + 1e-6: the rescaled spectrum leaves [-1, 1]");
     return KPM_EBOUNDS;
   }

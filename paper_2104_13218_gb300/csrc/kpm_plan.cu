@@ -63,9 +63,9 @@ int validate_sectors(const kpm_model *m, int n_sectors, const int32_t *n_up) {
 }
 
 int64_t choose_tile_states(int gpw, int64_t total_rows) {
-  // 64 block iterations of kWarps * gpw states, but at least ~4 tiles per SM
+  // 32 block iterations of kWarps * gpw states, but at least ~4 tiles per SM
   // for small problems (152 SMs).
-  int64_t big = (int64_t)64 * kWarps * gpw;
+  int64_t big = (int64_t)32 * kWarps * gpw;
   int64_t small = std::max<int64_t>((int64_t)kWarps * gpw, total_rows / (4 * 152));
   return std::max<int64_t>(1, std::min(big, small));
 }
@@ -76,6 +76,9 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
   KPM_TRY(validate_sectors(m, n_sectors, n_up));
   KPM_REQUIRE(tile_states >= 1, KPM_EINVAL, "tile_states < 1");
   const int N = m->n_sites;
+  for (int s = 0; s < n_sectors; ++s)
+    KPM_REQUIRE(n_up[s] >= 0 || N <= 32, KPM_EINVAL,
+                "the full 2^N space is limited to N <= 32 (ranks are 32-bit); use sectors");
   p->N = N;
   p->L = N / 2;
   p->H = N - p->L;
@@ -192,6 +195,55 @@ void fill_bonds(const kpm_model *m, BondsDev *out) {
     q += 0.25 * m->J[b];
   }
   out->J_quarter_sum = q;
+  // groups of equal couplings, in order of first appearance
+  std::vector<double> vals;
+  std::vector<int> gid(m->n_bonds);
+  for (int b = 0; b < m->n_bonds; ++b) {
+    int g = -1;
+    for (size_t v = 0; v < vals.size(); ++v)
+      if (vals[v] == m->J[b]) g = (int)v;
+    if (g < 0) {
+      g = (int)vals.size();
+      vals.push_back(m->J[b]);
+    }
+    gid[b] = g;
+  }
+  int64_t tsize = 1;
+  for (size_t g = 0; g < vals.size(); ++g) {
+    int cnt = 0;
+    for (int b = 0; b < m->n_bonds; ++b) cnt += gid[b] == (int)g;
+    tsize *= (cnt + 1);
+  }
+  for (int b = 0; b < m->n_bonds; ++b) out->order[b] = (uint8_t)b;
+  if (vals.size() > (size_t)kMaxGroups || tsize > kMaxDiagTable || m->n_bonds == 0) {
+    out->n_groups = 0;
+    out->table_size = 0;
+    return;
+  }
+  out->n_groups = (int32_t)vals.size();
+  int k = 0, stride = 1;
+  for (int g = 0; g < out->n_groups; ++g) {
+    out->gstart[g] = k;
+    out->tstride[g] = stride;
+    out->gJ[g] = vals[g];
+    for (int b = 0; b < m->n_bonds; ++b)
+      if (gid[b] == g) out->order[k++] = (uint8_t)b;
+    stride *= (k - out->gstart[g]) + 1;
+  }
+  out->gstart[out->n_groups] = k;
+  out->table_size = stride;
+}
+
+void fill_pass_masks(BondsDev *b, int G) {
+  b->G = G;
+  b->n_pass = G >= 2 ? (b->n_bonds + G - 1) / G : 0;
+  std::memset(b->pmask, 0, sizeof(b->pmask));
+  if (G < 2 || b->n_groups == 0) return;
+  for (int g = 0; g < b->n_groups; ++g)
+    for (int k = b->gstart[g]; k < b->gstart[g + 1]; ++k) {
+      const int bond = b->order[k];
+      b->pmask[bond / G][g] |= 1u << (bond % G);
+    }
 }
 
 size_t tables_bytes(const Plan &p) {

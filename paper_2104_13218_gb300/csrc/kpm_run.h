@@ -21,7 +21,30 @@ struct MomentsRun {
   double *sums = nullptr;      // [S][n_sectors][NQ]
   int *counters = nullptr;     // [2*S]: tile queue and finished-block count per step
   int *flag = nullptr;         // EBOUNDS flag
+  bool profile = true;         // bracket step launches with events when profiling
 };
+
+// The FP32 form stores sectors smaller than this in FP64: in a tiny sector the
+// +-1/sqrt(D) vectors keep few distinct magnitudes, FP32 rounding errors stay
+// coherent instead of averaging out, and they grow linearly with the order.
+constexpr int64_t kFP32MinSectorDim = 1024;
+
+// A kpm_moments call: the main run, plus (FP32 form only) an FP64 run of the
+// sectors below kFP32MinSectorDim.
+struct MomentsJob {
+  MomentsRun main, side;
+  bool has_main = false, has_side = false;
+  std::vector<int32_t> nup_main, nup_side;
+  std::vector<int> map_main, map_side;  // job sector -> caller sector
+  int n_sectors = 0, K = 0;
+};
+int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
+                int precision, MomentsJob *job);
+size_t job_bytes(const MomentsJob &job);
+int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, cudaStream_t s);
+// init + K/2 steps + assembly of both runs; flag_out receives the EBOUNDS flag address
+int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
+            cudaStream_t s);
 
 // Builds the plan and the layout; no device work.
 int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
@@ -30,9 +53,11 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
 size_t run_bytes(const MomentsRun &run);
 // Carves the run's buffers from the arena and uploads tables (a, b per sector).
 int setup_run(MomentsRun &run, const double *a, const double *b, Arena &arena,
-              cudaStream_t stream);
-// v0 <- random vectors r0 .. r0+R-1 (padding columns zero).
-int launch_init(const MomentsRun &run, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s);
+              cudaStream_t stream, const int *out_index = nullptr);
+// v0 <- random vectors r0 .. r0+R-1 (padding columns zero): signs +-1/sqrt(D), or
+// with `uniform` values uniform in (-1, 1) from the same hash (Lanczos start vectors).
+int launch_init(const MomentsRun &run, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s,
+                bool uniform = false);
 // One fused step.  first = 1: y = H' x (y written to zy, z not read).
 // first = 0: zy <- 2 H' x - zy.  Dot products of this step go to sums[step].
 int launch_step(const MomentsRun &run, const void *x, void *zy, int first, int step,

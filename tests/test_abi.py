@@ -77,11 +77,14 @@ def test_invalid_models_and_sectors_are_rejected():
 
 
 def test_workspace_sizes_scale_with_problem():
-    small = kpm.moments_workspace_size(W.ring(12), [6], 100, 8, "fp64")
-    big = kpm.moments_workspace_size(W.ring(12), [6], 100, 16, "fp64")
-    f32 = kpm.moments_workspace_size(W.ring(12), [6], 100, 16, "fp32")
+    small = kpm.moments_workspace_size(W.ring(14), [7], 100, 8, "fp64")
+    big = kpm.moments_workspace_size(W.ring(14), [7], 100, 16, "fp64")
+    f32 = kpm.moments_workspace_size(W.ring(14), [7], 100, 16, "fp32")
     assert big > small > 0
     assert f32 < big
+    # in the FP32 form a sector below 1024 states is stored in FP64
+    assert (kpm.moments_workspace_size(W.ring(12), [6], 100, 16, "fp32")
+            == kpm.moments_workspace_size(W.ring(12), [6], 100, 16, "fp64"))
     # two interleaved vectors of the ring-34 S^z = 0 sector in FP32 with R = 4
     cfg5 = kpm.moments_workspace_size(W.ring(34), [17], 2000, 4, "fp32")
     assert cfg5 >= 2 * 2333606220 * 4 * 4

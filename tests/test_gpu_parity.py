@@ -75,8 +75,8 @@ def test_ring10_full_space_fp64_matches_oracle():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
 def test_all_sectors_ragged_in_one_launch(precision, tol):
-    model = W.ring(12)
-    n_up = W.all_sectors(12)           # dims 1, 12, 66, ..., 924, ..., 1
+    model = W.ring(14)
+    n_up = W.all_sectors(14)           # dims 1, 14, 91, ..., 3432, ..., 1 (FP32: < 1024 in FP64)
     a, b = _exact_bounds(model, n_up, 0.025)
     gpu = kpm.moments(model, n_up, 64, 7, 11, a=a, b=b, precision=precision)
     ref = _oracle_runs(model, n_up, a, b, 64, 7, 11)
@@ -317,7 +317,13 @@ def test_autograd_matches_finite_differences():
     model = W.j1j2_chain(10, 1.0, 0.3)
     n_up = W.nonnegative_sectors(10)
     mirror = [0 if k == 5 else 1 for k in n_up]
-    a, b = _exact_bounds(model, n_up, 0.2)   # wide margin: the couplings move during FD
+    # fixed rescaling with a margin of 1 around every sector's spectrum: the couplings
+    # move during the finite differences (a one-state sector would otherwise get a ~ 0)
+    bi, bj, J = model.arrays()
+    ab = [O.rescale(O.eigenvalues(10, bi, bj, J, k).min() - 1.0,
+                    O.eigenvalues(10, bi, bj, J, k).max() + 1.0, 0.0) for k in n_up]
+    a = np.array([x[0] for x in ab])
+    b = np.array([x[1] for x in ab])
     T = W.log_grid(0.3, 5.0, 20)
     spec = dict(model=model, n_up=n_up, mirror=mirror, a=a, b=b, K=120, R=6, seed=3, T=T,
                 kernel="jackson", ckpt_interval=16)
