@@ -127,7 +127,7 @@ size_t kpm_bounds_workspace_size(const kpm_model *model, int32_t n_sectors, cons
  *                    if either is NULL, kpm_bounds is run first with eps,
  *                    100 Lanczos steps and tol 1e-8.
  *   n_moments     -- K, even, >= 2.
- *   R             -- random vectors per sector, 1 .. 512 (FP32) / 256 (FP64).
+ *   R             -- random vectors per sector, 1 .. 512.
  *   seed, r0      -- random-vector stream (see the conventions above).
  *   precision     -- KPM_FP64 or KPM_FP32.
  *   mu            -- [n_sectors][K] output (required).

@@ -228,7 +228,8 @@ void *pick_adj(int cpl, bool full) {
     case 1: return full ? adj_ptr<1, true>() : adj_ptr<1, false>();
     case 2: return full ? adj_ptr<2, true>() : adj_ptr<2, false>();
     case 3: return full ? adj_ptr<3, true>() : adj_ptr<3, false>();
-    default: return full ? adj_ptr<4, true>() : adj_ptr<4, false>();
+    case 4: return full ? adj_ptr<4, true>() : adj_ptr<4, false>();
+    default: return full ? adj_ptr<8, true>() : adj_ptr<8, false>();
   }
 }
 

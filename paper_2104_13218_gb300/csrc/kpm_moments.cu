@@ -36,6 +36,8 @@ struct StepArgs {
   double half_n;    // N/2
 };
 
+constexpr int kGB = 4;  // neighbour rows gathered per batch in the cooperative path
+
 template <typename T, int CPL, bool FULL>
 __global__ void __launch_bounds__(kThreads)
     cheb_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd) {
@@ -147,14 +149,15 @@ __global__ void __launch_bounds__(kThreads)
         for (int p = 0; p < bd.n_pass; ++p) {
           const int b = p * G + sub;
           bool fl = false;
-          uint32_t nr = 0;
+          uint32_t nc = 0;  // first 16-byte chunk of the neighbour's row (< 2^32, checked on the host)
           if (valid && b < nb) {
             const uint64_t m = bd.mask[b];
             const uint64_t tt = s & m;
             if (tt != 0 && tt != m) {
               fl = true;
               const uint64_t f = s ^ m;
-              nr = full_tile ? (uint32_t)f : sector_rank(f, a.tb);
+              const uint32_t rk = full_tile ? (uint32_t)f : sector_rank(f, a.tb);
+              nc = ((uint32_t)sd.row0 + rk) * (uint32_t)crow;
             }
           }
           const uint32_t F =
@@ -169,17 +172,29 @@ __global__ void __launch_bounds__(kThreads)
                 V gs[CPL];
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) gs[c] = V{};
-                for (int i = 0; i < nmax; ++i) {
-                  const int j = Fg ? __ffs(Fg) - 1 : 0;
-                  const uint32_t rk = __shfl_sync(0xffffffffu, nr, (gbase + j) & 31);
-                  if (Fg) {
-                    Fg &= Fg - 1;
-                    const V *src = x + (sd.row0 + (int64_t)rk) * crow + sub;
+                // batches of kGB neighbours: all shuffles, then all loads, then the sums
+                for (int i = 0; i < nmax; i += kGB) {
+                  uint32_t ci[kGB];
+                  bool ok[kGB];
+#pragma unroll
+                  for (int q = 0; q < kGB; ++q) {
+                    ok[q] = Fg != 0;
+                    const int j = ok[q] ? __ffs(Fg) - 1 : 0;
+                    ci[q] = __shfl_sync(0xffffffffu, nc, (gbase + j) & 31);
+                    if (ok[q]) Fg &= Fg - 1;
+                  }
+                  V v[kGB][CPL];
+#pragma unroll
+                  for (int q = 0; q < kGB; ++q) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) v[q][c] = ok[q] ? __ldg(x + ci[q] + sub + c * G) : V{};
+                  }
+#pragma unroll
+                  for (int q = 0; q < kGB; ++q) {
 #pragma unroll
                     for (int c = 0; c < CPL; ++c) {
-                      const V v = __ldg(src + c * G);
 #pragma unroll
-                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v, e));
+                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v[q][c], e));
                     }
                   }
                 }
@@ -200,13 +215,13 @@ __global__ void __launch_bounds__(kThreads)
             const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(Fb));
             for (int i = 0; i < nmax; ++i) {
               const int j = Fb ? __ffs(Fb) - 1 : 0;
-              const uint32_t rk = __shfl_sync(0xffffffffu, nr, (gbase + j) & 31);
+              const uint32_t cidx = __shfl_sync(0xffffffffu, nc, (gbase + j) & 31);
               if (Fb) {
                 Fb &= Fb - 1;
                 const int bb = p * G + j;
                 const T aj = s_aj[bb];
                 dsum += s_jh[bb];
-                const V *src = x + (sd.row0 + (int64_t)rk) * crow + sub;
+                const V *src = x + cidx + sub;
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                   const V v = __ldg(src + c * G);
@@ -525,14 +540,16 @@ void *pick_step(int precision, int cpl, bool full) {
       case 1: return full ? step_ptr<float, 1, true>() : step_ptr<float, 1, false>();
       case 2: return full ? step_ptr<float, 2, true>() : step_ptr<float, 2, false>();
       case 3: return full ? step_ptr<float, 3, true>() : step_ptr<float, 3, false>();
-      default: return full ? step_ptr<float, 4, true>() : step_ptr<float, 4, false>();
+      case 4: return full ? step_ptr<float, 4, true>() : step_ptr<float, 4, false>();
+      default: return full ? step_ptr<float, 8, true>() : step_ptr<float, 8, false>();
     }
   }
   switch (cpl) {
     case 1: return full ? step_ptr<double, 1, true>() : step_ptr<double, 1, false>();
     case 2: return full ? step_ptr<double, 2, true>() : step_ptr<double, 2, false>();
     case 3: return full ? step_ptr<double, 3, true>() : step_ptr<double, 3, false>();
-    default: return full ? step_ptr<double, 4, true>() : step_ptr<double, 4, false>();
+    case 4: return full ? step_ptr<double, 4, true>() : step_ptr<double, 4, false>();
+    default: return full ? step_ptr<double, 8, true>() : step_ptr<double, 8, false>();
   }
 }
 
@@ -571,6 +588,9 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   }
   KPM_TRY(build_plan(m, n_sectors, n_up, choose_tile_states(run->lay.gpw, rows), &run->plan));
   run->NQ = run->plan.any_full ? 6 : 2;
+  KPM_REQUIRE((uint64_t)run->plan.total_rows * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
+              KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
+              (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
   fill_bonds(m, &run->bonds);
   fill_pass_masks(&run->bonds, run->lay.G);
   run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);

@@ -324,8 +324,9 @@ int make_layout(int R, int precision, RowLayout *o) {
   o->vec_width = precision == KPM_FP32 ? 4 : 2;
   o->elem = precision == KPM_FP32 ? 4 : 8;
   o->chunks = (R + o->vec_width - 1) / o->vec_width;
+  KPM_REQUIRE(R <= 512, KPM_EINVAL, "R = %d too large (max 512)", R);
   o->cpl = (o->chunks + 31) / 32;
-  KPM_REQUIRE(o->cpl <= 4, KPM_EINVAL, "R = %d too large (max %d)", R, 128 * o->vec_width);
+  if (o->cpl > 4) o->cpl = 8;  // chunks-per-lane layouts: 1, 2, 3, 4, 8
   o->G = (o->chunks + o->cpl - 1) / o->cpl;
   o->gpw = 32 / o->G;
   o->Rp = o->G * o->cpl * o->vec_width;

@@ -46,7 +46,7 @@ def _model_struct(model):
     return kpm.CModel.of(model)
 
 
-@pytest.mark.parametrize("K,R,prec", [(3, 4, 0), (0, 4, 0), (10, 0, 0), (10, 600, 1), (10, 300, 0),
+@pytest.mark.parametrize("K,R,prec", [(3, 4, 0), (0, 4, 0), (10, 0, 0), (10, 600, 1), (10, 513, 0),
                                       (10, 4, 7)])
 def test_moments_rejects_bad_sizes(K, R, prec):
     m = _model_struct(W.ring(8))
