@@ -220,6 +220,38 @@ size_t kpm_moments_backward_workspace_size(const kpm_model *model, int32_t n_sec
                                            int32_t R, int32_t ckpt_interval);
 
 /*
+ * kpm_moments_static -- kpm_moments without any device allocation.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc: applications whose framework reserves the device
+ * memory up front in its own pool (where a further cudaMalloc fails or
+ * fragments the pool), and latency-critical loops that must stay out of the
+ * CUDA allocator (cudaFree waits for the whole device).  It computes exactly
+ * what kpm_moments computes, with the same kernels, but takes its scratch
+ * from a fixed array of kpm_static_scratch_bytes() bytes (64 MiB) compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.
+ *   a, b         -- host [n_sectors] rescaling (required: no bound estimate is run).
+ *   mu, mu_M, mu_M2 -- DEVICE arrays [n_sectors][K] (mu_M, mu_M2 may be NULL).
+ *   other arguments as in kpm_moments.
+ * Returns KPM_ENOMEM, with the needed size in kpm_last_error(), when the
+ * problem's scratch (kpm_moments_workspace_size) exceeds the array.  The
+ * first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  All calls share the array and every call
+ * clears the parts that must start at zero; calls whose work overlaps on the
+ * GPU (different streams or threads) race on it and must be serialised by
+ * the caller.
+ */
+int kpm_moments_static(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
+                       const double *a, const double *b, int32_t n_moments, int32_t R,
+                       uint64_t seed, uint64_t r0, int32_t precision, double *mu, double *mu_M,
+                       double *mu_M2, void *stream);
+
+/* Size in bytes of the fixed scratch array behind kpm_moments_static. */
+size_t kpm_static_scratch_bytes(void);
+
+/*
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  * kpm_profile_enable(1) starts recording a CUDA event pair around every
  * launch of the fused Chebyshev step kernel, on the stream it is launched

@@ -57,6 +57,9 @@ PROTOTYPES = {
                                        c_uint64, c_int32, c_int32, P, P, P, P, c_int32, P, c_size_t,
                                        P]),
     "kpm_moments_backward_workspace_size": (c_size_t, [P, c_int32, P, c_int32, c_int32, c_int32]),
+    "kpm_moments_static": (c_int32, [P, c_int32, P, P, P, c_int32, c_int32, c_uint64, c_uint64,
+                                     c_int32, P, P, P, P]),
+    "kpm_static_scratch_bytes": (c_size_t, []),
     "kpm_profile_enable": (c_int32, [c_int32]),
     "kpm_profile_read": (c_int32, [P, P, P]),
 }
