@@ -40,12 +40,88 @@ __device__ __forceinline__ uint64_t sector_unrank(uint32_t r, int k, uint32_t b_
   return ((uint64_t)hi << tb.L) | lo;
 }
 
+// Bitstring of rank r in sector k by binary search over the hi-blocks
+// [b_lo, b_hi] (the block holding r is among them).
+__device__ __forceinline__ uint64_t sector_unrank_search(uint32_t r, int k, uint32_t b_lo,
+                                                         uint32_t b_hi, const TablesDev &tb) {
+  while (b_lo < b_hi) {
+    const uint32_t mid = (b_lo + b_hi + 1) >> 1;
+    if (__ldg(tb.hb_off + mid) <= r)
+      b_lo = mid;
+    else
+      b_hi = mid - 1;
+  }
+  const uint32_t hi = __ldg(tb.hb_hi + b_lo);
+  const int c = k - __popc(hi);
+  const uint32_t lo = __ldg(tb.lo_list + __ldg(tb.lo_start + c) + (r - __ldg(tb.hb_off + b_lo)));
+  return ((uint64_t)hi << tb.L) | lo;
+}
+
+// Next larger integer with the same number of set bits (s != 0): the state of
+// rank r + 1 in a sector, from the state of rank r.
+__device__ __forceinline__ uint64_t next_same_popcount(uint64_t s) {
+  const uint64_t t = s | (s - 1);
+  const uint64_t nt = ~t;
+  return (t + 1) | (((nt & (0 - nt)) - 1) >> (__ffsll((long long)s)));
+}
+
+// Packed two-wide FP32 arithmetic (PTX f32x2, sm_100 and later): one
+// instruction updates two floats held in a 64-bit register pair.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+  return *reinterpret_cast<unsigned long long *>(&v);
+}
+__device__ __forceinline__ float2 f2_from(unsigned long long r) {
+  return *reinterpret_cast<float2 *>(&r);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return f2_from(d);
+}
+
+// A 16-byte chunk of a row with the element-wise operations of the step.
 template <typename T>
 struct Chunk;
 template <>
 struct Chunk<float> {
   using type = float4;
   static constexpr int W = 4;
+  __device__ static __forceinline__ float2 lo(const float4 &v) { return make_float2(v.x, v.y); }
+  __device__ static __forceinline__ float2 hi(const float4 &v) { return make_float2(v.z, v.w); }
+  __device__ static __forceinline__ float4 join(float2 l, float2 h) { return make_float4(l.x, l.y, h.x, h.y); }
+  // acc + v
+  __device__ static __forceinline__ float4 add(const float4 &acc, const float4 &v) {
+    return join(add2(lo(acc), lo(v)), add2(hi(acc), hi(v)));
+  }
+  // s * v + acc
+  __device__ static __forceinline__ float4 fma(float s, const float4 &v, const float4 &acc) {
+    const float2 ss = make_float2(s, s);
+    return join(fma2(ss, lo(v), lo(acc)), fma2(ss, hi(v), hi(acc)));
+  }
+  // s * v + acc - z
+  __device__ static __forceinline__ float4 fma_sub(float s, const float4 &v, const float4 &acc,
+                                                   const float4 &z) {
+    const float2 ss = make_float2(s, s);
+    return join(sub2(fma2(ss, lo(v), lo(acc)), lo(z)), sub2(fma2(ss, hi(v), hi(acc)), hi(z)));
+  }
+  // running dot products: p_aa += a.a, p_ba += b.a (two lanes of partial sums each)
+  __device__ static __forceinline__ void dots(const float4 &a, const float4 &b, float2 &paa,
+                                              float2 &pba) {
+    paa = fma2(lo(a), lo(a), paa);
+    paa = fma2(hi(a), hi(a), paa);
+    pba = fma2(lo(b), lo(a), pba);
+    pba = fma2(hi(b), hi(a), pba);
+  }
   __device__ static __forceinline__ float get(const float4 &v, int i) {
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
   }
@@ -57,6 +133,23 @@ template <>
 struct Chunk<double> {
   using type = double2;
   static constexpr int W = 2;
+  __device__ static __forceinline__ double2 add(const double2 &acc, const double2 &v) {
+    return make_double2(acc.x + v.x, acc.y + v.y);
+  }
+  __device__ static __forceinline__ double2 fma(double s, const double2 &v, const double2 &acc) {
+    return make_double2(::fma(s, v.x, acc.x), ::fma(s, v.y, acc.y));
+  }
+  __device__ static __forceinline__ double2 fma_sub(double s, const double2 &v, const double2 &acc,
+                                                    const double2 &z) {
+    return make_double2(::fma(s, v.x, acc.x) - z.x, ::fma(s, v.y, acc.y) - z.y);
+  }
+  __device__ static __forceinline__ void dots(const double2 &a, const double2 &b, double2 &paa,
+                                              double2 &pba) {
+    paa.x = ::fma(a.x, a.x, paa.x);
+    paa.y = ::fma(a.y, a.y, paa.y);
+    pba.x = ::fma(b.x, a.x, pba.x);
+    pba.y = ::fma(b.y, a.y, pba.y);
+  }
   __device__ static __forceinline__ double get(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
   __device__ static __forceinline__ void set(double2 &v, int i, double x) {
     if (i == 0) v.x = x; else v.y = x;

@@ -17,6 +17,7 @@
 // depend on the schedule.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "kpm_device.cuh"
@@ -38,8 +39,13 @@ struct StepArgs {
 
 constexpr int kGB = 4;  // neighbour rows gathered per batch in the cooperative path
 
+// Minimum resident blocks per SM requested from the compiler for the step kernel.
+#ifndef KPM_STEP_MIN_BLOCKS
+#define KPM_STEP_MIN_BLOCKS 3
+#endif
+
 template <typename T, int CPL, bool FULL>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
     cheb_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd) {
   using C = Chunk<T>;
   using V = typename C::type;
@@ -123,18 +129,53 @@ __global__ void __launch_bounds__(kThreads)
     const bool coop = G >= 2;
     const int gbase = grp * G;  // first lane of this lane's group (idle lanes: past the groups)
     const uint32_t gmaskG = G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
+    // Which states this warp visits.  Cooperative layouts: a contiguous run of
+    // the tile per warp (groups of the warp take consecutive states), so that a
+    // group steps to its next state arithmetically when gpw <= 4; one-lane
+    // layouts: the warp's 32 lanes take 32 consecutive states per iteration.
+    uint32_t u_begin, u_end, u_step;
+    if (coop) {
+      const uint32_t per = ((tile.count + kWarps - 1) / kWarps + a.gpw - 1) / a.gpw * a.gpw;
+      u_begin = min(tile.count, warp * per);
+      u_end = min(tile.count, u_begin + per);
+      u_step = a.gpw;
+    } else {
+      u_begin = warp * a.gpw;
+      u_end = tile.count;
+      u_step = kWarps * a.gpw;
+    }
+    const bool stepping = coop && a.gpw <= 4 && !full_tile;
+    uint64_t s_next = 0;
+    if (stepping && active && u_begin + grp < u_end)
+      s_next = sector_unrank_search(tile.rank0 + u_begin + grp, sd.n_up, tile.b_first, tile.b_last,
+                                    a.tb);
     // Warp-uniform loop over the warp's states, so that ballots and shuffles see all lanes.
-    for (uint32_t ub = warp * a.gpw; ub < tile.count; ub += kWarps * a.gpw) {
+    for (uint32_t ub = u_begin; ub < u_end; ub += u_step) {
       const uint32_t u = ub + grp;
-      const bool valid = active && u < tile.count;
+      const bool valid = active && u < u_end;
       uint64_t s = 0;
       int64_t row = 0;
+      V xv[CPL], zv[CPL];
       if (valid) {
         row = tile.row0 + u;
-        if (full_tile)
+        if (full_tile) {
           s = (uint64_t)(row - sd.row0);
-        else
+        } else if (stepping) {
+          s = s_next;
+          uint64_t t = s;
+          for (int i = 0; i < a.gpw; ++i) t = next_same_popcount(t);
+          s_next = t;
+        } else {
           s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+        }
+        // own rows early: their latency overlaps the bond pass and the gathers
+        const V *xo = x + row * crow + sub;
+        const V *zo = zy + row * crow + sub;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          xv[c] = xo[c * G];
+          zv[c] = a.first ? V{} : __ldcs(zo + c * G);
+        }
       }
       V acc[CPL];
 #pragma unroll
@@ -192,21 +233,14 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
                   for (int q = 0; q < kGB; ++q) {
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-#pragma unroll
-                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v[q][c], e));
-                    }
+                    for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
                   }
                 }
                 const T gh = s_gh[g], gl = s_gl[g];
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-#pragma unroll
-                  for (int e = 0; e < W; ++e) {
-                    T v = fma(gh, C::get(gs[c], e), C::get(acc[c], e));
-                    if (PAIR) v = fma(gl, C::get(gs[c], e), v);
-                    C::set(acc[c], e, v);
-                  }
+                  acc[c] = C::fma(gh, gs[c], acc[c]);
+                  if (PAIR) acc[c] = C::fma(gl, gs[c], acc[c]);
                 }
               }
             }
@@ -223,12 +257,7 @@ __global__ void __launch_bounds__(kThreads)
                 dsum += s_jh[bb];
                 const V *src = x + cidx + sub;
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                  const V v = __ldg(src + c * G);
-#pragma unroll
-                  for (int e = 0; e < W; ++e)
-                    C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
-                }
+                for (int c = 0; c < CPL; ++c) acc[c] = C::fma(aj, __ldg(src + c * G), acc[c]);
               }
             }
           }
@@ -274,11 +303,7 @@ __global__ void __launch_bounds__(kThreads)
                     ++cnt;
                     const V *src = x + nrow[j] * crow + sub;
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                      const V v = __ldg(src + c * G);
-#pragma unroll
-                      for (int e = 0; e < W; ++e) C::set(gs[c], e, C::get(gs[c], e) + C::get(v, e));
-                    }
+                    for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], __ldg(src + c * G));
                   }
                 }
               }
@@ -286,12 +311,8 @@ __global__ void __launch_bounds__(kThreads)
               const T gh = s_gh[g], gl = s_gl[g];
 #pragma unroll
               for (int c = 0; c < CPL; ++c) {
-#pragma unroll
-                for (int e = 0; e < W; ++e) {
-                  T v = fma(gh, C::get(gs[c], e), C::get(acc[c], e));
-                  if (PAIR) v = fma(gl, C::get(gs[c], e), v);
-                  C::set(acc[c], e, v);
-                }
+                acc[c] = C::fma(gh, gs[c], acc[c]);
+                if (PAIR) acc[c] = C::fma(gl, gs[c], acc[c]);
               }
             }
           }
@@ -324,12 +345,7 @@ __global__ void __launch_bounds__(kThreads)
                 const T aj = s_aj[b0 + j];
                 const V *src = x + nrow[j] * crow + sub;
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                  const V v = __ldg(src + c * G);
-#pragma unroll
-                  for (int e = 0; e < W; ++e)
-                    C::set(acc[c], e, fma(aj, C::get(v, e), C::get(acc[c], e)));
-                }
+                for (int c = 0; c < CPL; ++c) acc[c] = C::fma(aj, __ldg(src + c * G), acc[c]);
               }
             }
           }
@@ -337,27 +353,18 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       if (valid) {
-        const V *xo = x + row * crow + sub;
         V *zo = zy + row * crow + sub;
-        T pxx = 0, pyx = 0;
+        using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        P2 paa{}, pba{};
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          const V xv = xo[c * G];
-          V zv = V{};
-          if (!a.first) zv = __ldcs(zo + c * G);
-          V y;
-#pragma unroll
-          for (int e = 0; e < W; ++e) {
-            const T xe = C::get(xv, e);
-            T h = C::get(acc[c], e);
-            if (PAIR) h = fma(ad_lo, xe, h);
-            const T ye = fma(ad_hi, xe, h) - C::get(zv, e);
-            C::set(y, e, ye);
-            pxx = fma(xe, xe, pxx);
-            pyx = fma(ye, xe, pyx);
-          }
+          V h = acc[c];
+          if (PAIR) h = C::fma(ad_lo, xv[c], h);
+          const V y = C::fma_sub(ad_hi, xv[c], h, zv[c]);
+          C::dots(xv[c], y, paa, pba);
           __stcs(zo + c * G, y);
         }
+        const T pxx = paa.x + paa.y, pyx = pba.x + pba.y;
         if constexpr (sizeof(T) == 8) {
           acc64[0] += pxx;
           acc64[1] += pyx;

@@ -326,6 +326,9 @@ int make_layout(int R, int precision, RowLayout *o) {
   o->chunks = (R + o->vec_width - 1) / o->vec_width;
   KPM_REQUIRE(R <= 512, KPM_EINVAL, "R = %d too large (max 512)", R);
   o->cpl = (o->chunks + 31) / 32;
+#ifdef KPM_MIN_CPL
+  if (o->chunks >= 2 * KPM_MIN_CPL && o->cpl < KPM_MIN_CPL) o->cpl = KPM_MIN_CPL;
+#endif
   if (o->cpl > 4) o->cpl = 8;  // chunks-per-lane layouts: 1, 2, 3, 4, 8
   o->G = (o->chunks + o->cpl - 1) / o->cpl;
   o->gpw = 32 / o->G;
