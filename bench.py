@@ -215,6 +215,8 @@ def run_ours(args):
     import paper_2104_13218_gb300 as kpm
     from paper_2104_13218_gb300 import _lib
 
+    from paper_2104_13218_gb300.replicas import combine_moments, vector_offset
+
     rank, world, local = env_rank()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -226,7 +228,7 @@ def run_ours(args):
     precision = args.precision or ("fp32" if "fp32" in w.precisions else "fp64")
     units, total_rows = units_per_step(w)
     L = kpm.lib()
-    r0 = rank * w.R
+    r0 = vector_offset(rank, w.R)
     secs_T = w.T
     mirror = w.mirror
 
@@ -244,10 +246,7 @@ def run_ours(args):
             mom = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=bnd["a"], b=bnd["b"], r0=r0,
                               precision=prec, device=True, out=out, workspace=ws_m,
                               allow_ebounds=True)
-            if world > 1:
-                for k in ("mu", "mu_M", "mu_M2"):
-                    dist.all_reduce(mom[k])
-                    mom[k] /= world
+            combine_moments(mom, world)
             secs = kpm.sector_set(w.model.n_sites, w.n_up, bnd["a"], bnd["b"], mirror)
             return kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, secs_T, kernel=w.kernel)
         return step
@@ -324,10 +323,9 @@ def run_ours(args):
         mom = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=bnd["a"], b=bnd["b"], r0=r0,
                           precision=precision, allow_ebounds=True)
         if world > 1:
-            for k in ("mu", "mu_M", "mu_M2"):
-                t = torch.from_numpy(mom[k]).to(dev)
-                dist.all_reduce(t)
-                mom[k] = (t / world).cpu().numpy()
+            dm = combine_moments({k: torch.from_numpy(mom[k]).to(dev) for k in ("mu", "mu_M", "mu_M2")},
+                                 world)
+            mom.update({k: v.cpu().numpy() for k, v in dm.items()})
         secs = kpm.sector_set(w.model.n_sites, w.n_up, bnd["a"], bnd["b"], mirror)
         th = kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, secs_T, kernel=w.kernel)
         return th
