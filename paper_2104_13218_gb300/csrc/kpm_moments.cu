@@ -425,6 +425,241 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
   }
 }
 
+// ---------------------------------------------------------------- neighbour lists
+// The structure of H' does not change during a run: for every basis state the
+// anti-aligned bonds and the ranks of the bit-flipped neighbours are found
+// once, here, and stored as the state's neighbour list; the list step kernel
+// then reads them instead of recomputing bitstrings and ranks at every step.
+struct ListArgs {
+  uint32_t *lists;
+  TablesDev tb;
+  int stride;
+  uint32_t crow;  // 16-byte chunks per row
+};
+
+__global__ void __launch_bounds__(kThreads)
+    build_lists_kernel(const __grid_constant__ ListArgs a, const __grid_constant__ BondsDev bd) {
+  for (int t = blockIdx.x; t < a.tb.n_tiles; t += gridDim.x) {
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const bool full_tile = sd.n_up < 0;
+    uint32_t hb = tile.b_first;
+    for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
+      const int64_t row = tile.row0 + u;
+      const uint64_t s = full_tile ? (uint64_t)(row - sd.row0)
+                                   : sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+      uint32_t *L = a.lists + (size_t)row * a.stride;
+      uint32_t hdr = 0;
+      int e = 1;
+      for (int g = 0; g < bd.n_groups; ++g) {
+        uint32_t cnt = 0;
+        for (int k = bd.gstart[g]; k < bd.gstart[g + 1]; ++k) {
+          const uint64_t m = bd.mask[bd.order[k]];
+          const uint64_t tt = s & m;
+          if (tt != 0 && tt != m) {
+            const uint64_t f = s ^ m;
+            const uint32_t rk = full_tile ? (uint32_t)f : sector_rank(f, a.tb);
+            L[e++] = ((uint32_t)sd.row0 + rk) * a.crow;
+            ++cnt;
+          }
+        }
+        hdr |= cnt << (8 * g);
+      }
+      L[0] = hdr;
+    }
+  }
+}
+
+// Neighbour rows gathered per batch in the list kernel.
+#ifndef KPM_LIST_BATCH
+#define KPM_LIST_BATCH 4
+#endif
+
+// One Chebyshev step driven by the neighbour lists (cooperative layouts with
+// grouped couplings).  The G lanes of a state read the same list words (one
+// broadcast load each) and gather their own chunks of the listed rows.
+template <typename T, int CPL, bool FULL>
+__global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
+    cheb_step_list_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd,
+                          const uint32_t *__restrict__ lists, int stride) {
+  using C = Chunk<T>;
+  using V = typename C::type;
+  constexpr int NQ = FULL ? 6 : 2;
+  constexpr bool PAIR = sizeof(T) == 4;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  T *s_dh = reinterpret_cast<T *>(s_dyn);
+  T *s_dl = s_dh + bd.table_size;
+  __shared__ T s_gh[kMaxGroups], s_gl[kMaxGroups];
+  __shared__ double s_red[kWarps * NQ];
+  __shared__ int s_tile, s_last, s_sec;
+
+  const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
+  V *__restrict__ zy = reinterpret_cast<V *>(a.zy);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = a.G, gpw = a.gpw;
+  const int grp = lane / G, sub = lane - grp * G;
+  const bool active = grp < gpw;
+  const uint32_t crow = (uint32_t)(a.Rp / C::W);
+  const int ng = bd.n_groups;
+  if (threadIdx.x == 0) s_sec = -1;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.tb.n_tiles) break;
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    if (s_sec != tile.sector) {
+      __syncthreads();
+      const double A = (a.first ? 1.0 : 2.0) * sd.inv_a;
+      if (threadIdx.x < ng) {
+        const double c = A * 0.5 * bd.gJ[threadIdx.x];
+        const T hi = (T)c;
+        s_gh[threadIdx.x] = hi;
+        s_gl[threadIdx.x] = PAIR ? (T)(c - (double)hi) : (T)0;
+      }
+      for (int idx = threadIdx.x; idx < bd.table_size; idx += kThreads) {
+        double d = bd.J_quarter_sum;
+        for (int g = 0; g < ng; ++g) {
+          const int size = bd.gstart[g + 1] - bd.gstart[g];
+          d -= ((idx / bd.tstride[g]) % (size + 1)) * (0.5 * bd.gJ[g]);
+        }
+        const double ad = A * (d - sd.b);
+        const T hi = (T)ad;
+        s_dh[idx] = hi;
+        if (PAIR) s_dl[idx] = (T)(ad - (double)hi);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_sec = tile.sector;
+    }
+    __syncthreads();
+
+    double acc64[NQ];
+    KahanF accf[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc64[q] = 0.0;
+    if (active) {
+      const uint32_t per = ((tile.count + kWarps - 1) / kWarps + gpw - 1) / gpw * gpw;
+      const uint32_t u_begin = min(tile.count, warp * per);
+      const uint32_t u_end = min(tile.count, u_begin + per);
+      for (uint32_t u = u_begin + grp; u < u_end; u += gpw) {
+        const int64_t row = tile.row0 + u;
+        const uint32_t own = (uint32_t)row * crow + sub;
+        V xv[CPL], zv[CPL], acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          xv[c] = x[own + c * G];
+          zv[c] = a.first ? V{} : __ldcs(zy + own + c * G);
+          acc[c] = V{};
+        }
+        const uint32_t *L = lists + (size_t)row * stride;
+        const uint32_t hdr = __ldg(L);
+        int e = 1, tidx = 0;
+        for (int g = 0; g < ng; ++g) {
+          const int cnt = (hdr >> (8 * g)) & 255u;
+          tidx += cnt * bd.tstride[g];
+          V gs[CPL];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) gs[c] = V{};
+          constexpr int B = KPM_LIST_BATCH;
+          for (int i = 0; i < cnt; i += B) {
+            uint32_t ci[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? __ldg(L + e + i + q) : 0u;
+            V v[B][CPL];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+            }
+          }
+          e += cnt;
+          const T gh = s_gh[g], gl = s_gl[g];
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            acc[c] = C::fma(gh, gs[c], acc[c]);
+            if (PAIR) acc[c] = C::fma(gl, gs[c], acc[c]);
+          }
+        }
+        const T ad_hi = s_dh[tidx];
+        const T ad_lo = PAIR ? s_dl[tidx] : (T)0;
+        using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        P2 paa{}, pba{};
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          V h = acc[c];
+          if (PAIR) h = C::fma(ad_lo, xv[c], h);
+          const V y = C::fma_sub(ad_hi, xv[c], h, zv[c]);
+          C::dots(xv[c], y, paa, pba);
+          __stcs(zy + own + c * G, y);
+        }
+        const T pxx = paa.x + paa.y, pyx = pba.x + pba.y;
+        if constexpr (sizeof(T) == 8) {
+          acc64[0] += pxx;
+          acc64[1] += pyx;
+          if (FULL) {
+            const double M = sd.n_up < 0 ? (double)__popcll((uint64_t)(row - sd.row0)) - a.half_n : sd.Mval;
+            acc64[2] += M * pxx;
+            acc64[3] += M * pyx;
+            acc64[4] += M * M * pxx;
+            acc64[5] += M * M * pyx;
+          }
+        } else {
+          accf[0].add(pxx);
+          accf[1].add(pyx);
+          if (FULL) {
+            const float M = sd.n_up < 0 ? (float)__popcll((uint64_t)(row - sd.row0)) - (float)a.half_n
+                                        : (float)sd.Mval;
+            accf[2].add(M * pxx);
+            accf[3].add(M * pyx);
+            accf[4].add(M * M * pxx);
+            accf[5].add(M * M * pyx);
+          }
+        }
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc64[q] = accf[q].value();
+    }
+    block_sum<NQ>(acc64, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) a.partials[(int64_t)t * NQ + q] = acc64[q];
+    }
+  }
+
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int sec = warp; sec < a.tb.n_sectors; sec += kWarps) {
+      const int t0 = a.tb.tile_begin[sec], t1 = a.tb.tile_end[sec];
+      double v[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+      for (int tt = t0 + lane; tt < t1; tt += 32) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] += __ldcg(a.partials + (int64_t)tt * NQ + q);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a.sums[sec * NQ + q] = v[q];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- random vectors
 
 struct InitArgs {
@@ -541,6 +776,27 @@ void *step_ptr() {
   return reinterpret_cast<void *>(&cheb_step_kernel<T, CPL, FULL>);
 }
 
+void *pick_step(int precision, int cpl, bool full);
+
+template <typename T, int CPL, bool FULL>
+void *list_ptr() {
+  return reinterpret_cast<void *>(&cheb_step_list_kernel<T, CPL, FULL>);
+}
+
+void *pick_list(int precision, int cpl, bool full) {
+  if (precision == KPM_FP32) {
+    if (cpl == 1) return full ? list_ptr<float, 1, true>() : list_ptr<float, 1, false>();
+    return full ? list_ptr<float, 2, true>() : list_ptr<float, 2, false>();
+  }
+  if (cpl == 1) return full ? list_ptr<double, 1, true>() : list_ptr<double, 1, false>();
+  return full ? list_ptr<double, 2, true>() : list_ptr<double, 2, false>();
+}
+
+void *pick_kernel(const MomentsRun &r) {
+  if (r.list_stride > 0) return pick_list(r.precision, r.lay.cpl, r.plan.any_full);
+  return pick_step(r.precision, r.lay.cpl, r.plan.any_full);
+}
+
 void *pick_step(int precision, int cpl, bool full) {
   if (precision == KPM_FP32) {
     switch (cpl) {
@@ -600,6 +856,11 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
               (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
   fill_bonds(m, &run->bonds);
   fill_pass_masks(&run->bonds, run->lay.G);
+  // neighbour lists for cooperative layouts with grouped couplings (CPL 1 or 2)
+  run->list_stride = 0;
+  if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
+      m->n_bonds <= 255)
+    run->list_stride = m->n_bonds + 1;
   run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);
   (void)full;
   return KPM_OK;
@@ -607,6 +868,7 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
 
 size_t run_bytes(const MomentsRun &r) {
   return 2 * r.vec_bytes + tables_bytes(r.plan) +
+         align256((size_t)r.plan.total_rows * r.list_stride * sizeof(uint32_t)) +
          align256(r.plan.tiles.size() * r.NQ * sizeof(double)) +
          align256((size_t)r.S * r.plan.n_sectors * r.NQ * sizeof(double)) +
          align256((size_t)2 * r.S * sizeof(int)) + 256;
@@ -637,9 +899,22 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     sec[i].pad2 = 0;
   }
   KPM_TRY(upload_tables(r.plan, sec, arena, s, &r.tb));
+  if (r.list_stride > 0) {
+    r.lists = arena.take<uint32_t>((size_t)r.plan.total_rows * r.list_stride);
+    KPM_REQUIRE(r.lists != nullptr, KPM_ENOMEM, "workspace too small for the neighbour lists");
+    ListArgs la;
+    la.lists = r.lists;
+    la.tb = r.tb;
+    la.stride = r.list_stride;
+    la.crow = (uint32_t)(r.lay.Rp / r.lay.vec_width);
+    const int grid = (int)std::min<int64_t>((int64_t)r.plan.tiles.size(), (int64_t)8 * sm_count());
+    build_lists_kernel<<<grid, kThreads, 0, s>>>(la, r.bonds);
+    KPM_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
   KPM_CUDA(cudaMemsetAsync(r.counters, 0, sizeof(int) * 2 * r.S, s));
   KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
-  void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
+  void *fn = pick_kernel(r);
   int per_sm = 0;
   KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, step_smem(r)));
   per_sm = std::max(per_sm, 1);
@@ -684,8 +959,12 @@ int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int ste
   a.gpw = r.lay.gpw;
   a.first = first;
   a.half_n = 0.5 * r.plan.N;
-  void *fn = pick_step(r.precision, r.lay.cpl, r.plan.any_full);
-  void *args[] = {(void *)&a, (void *)&r.bonds};
+  void *fn = pick_kernel(r);
+  const uint32_t *lists = r.lists;
+  int stride = r.list_stride;
+  void *args_q[] = {(void *)&a, (void *)&r.bonds};
+  void *args_l[] = {(void *)&a, (void *)&r.bonds, (void *)&lists, (void *)&stride};
+  void **args = r.list_stride > 0 ? args_l : args_q;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const bool prof = r.profile && profiling();
   if (prof) {

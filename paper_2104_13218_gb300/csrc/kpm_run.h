@@ -22,6 +22,12 @@ struct MomentsRun {
   int *counters = nullptr;     // [2*S]: tile queue and finished-block count per step
   int *flag = nullptr;         // EBOUNDS flag
   bool profile = true;         // bracket step launches with events when profiling
+  // Neighbour lists (cooperative layouts with grouped couplings): per state,
+  // list_stride words: a header with the number of anti-aligned bonds of each
+  // coupling group (8 bits per group), then the first 16-byte chunk index of
+  // each bit-flipped neighbour's row, group by group.  Built once per run.
+  int list_stride = 0;         // 0: no lists (the step works matrix-free)
+  uint32_t *lists = nullptr;
 };
 
 // The FP32 form stores sectors smaller than this in FP64: in a tiny sector the
