@@ -470,9 +470,13 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Neighbour rows gathered per batch in the list kernel.
-#ifndef KPM_LIST_BATCH
-#define KPM_LIST_BATCH 4
+// Neighbour rows gathered per batch in the list kernel (FP32 / FP64 rows):
+// measured on the benchmark workloads, 8 suits FP32 and 4 suits FP64.
+#ifndef KPM_LIST_BATCH_F32
+#define KPM_LIST_BATCH_F32 8
+#endif
+#ifndef KPM_LIST_BATCH_F64
+#define KPM_LIST_BATCH_F64 4
 #endif
 
 // One Chebyshev step driven by the neighbour lists (cooperative layouts with
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
           V gs[CPL];
 #pragma unroll
           for (int c = 0; c < CPL; ++c) gs[c] = V{};
-          constexpr int B = KPM_LIST_BATCH;
+          constexpr int B = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
           for (int i = 0; i < cnt; i += B) {
             uint32_t ci[B];
 #pragma unroll
