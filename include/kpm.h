@@ -101,10 +101,12 @@ int64_t kpm_sector_dim(int32_t n_sites, int32_t n_up);
  * The paper rescales H into [-1 + eps/2, 1 - eps/2] with
  * a = (Emax - Emin)/(2 - eps) and b = (Emax + Emin)/2 (Eq. E-2-3, E-2-4)
  * and obtains extremal energies with the Lanczos method (Sec. 3.1.2).  This
- * call runs max_iter Lanczos steps in FP64 on the GPU for every sector at
- * once (two independent start vectors per sector, drawn like the moment
- * vectors from `seed`), widens the extreme Ritz values by their residual
- * bounds, and returns per sector (host arrays of n_sectors entries):
+ * call runs up to max_iter Lanczos steps in FP64 on the GPU for every sector
+ * at once (two independent start vectors per sector with components uniform
+ * in (-1, 1) from `seed`), in chunks of 16 steps, stopping after the first
+ * chunk at which every extreme Ritz value's residual bound is within tol
+ * (relative to max(1, |E|)); it widens the extreme Ritz values by their
+ * residual bounds and returns per sector (host arrays of n_sectors entries):
  *   e_min, e_max  -- the widened extremal eigenvalue estimates (may be NULL);
  *   a, b          -- the rescaling of Eq. E-2-4 from them.  A sector whose
  *                    spectrum is one point gets a = 1e-12 * max(1, |b|).

@@ -299,68 +299,86 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   std::swap(P, Q);  // Q = q_0
   KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));  // q_{-1} = 0
   la.breakdown = 1e-12 * std::max(1.0, jabs);
-  for (int j = 0; j < max_iter; ++j) {
-    for (int mode = 1; mode <= 3; ++mode) {
-      la.P = P;
-      la.Q = Q;
-      la.mode = mode;
-      la.queue = counters + 4 * j + (mode == 1 ? 0 : (mode == 2 ? 2 : 0));
-      la.done = la.queue + 1;
-      if (mode == 3) la.queue = counters + 4 * kMaxLanczos;  // reset below
-      la.coef = mode == 1 ? beta + (size_t)j * n_sectors * 2
-                          : (mode == 2 ? alpha + (size_t)j * n_sectors * 2
-                                       : beta + (size_t)(j + 1) * n_sectors * 2);
-      la.out = mode == 1 ? alpha + (size_t)j * n_sectors * 2 : beta + (size_t)(j + 1) * n_sectors * 2;
-      if (mode == 3) KPM_CUDA(cudaMemsetAsync(la.queue, 0, sizeof(int) * 2, stream));
-      void *args[] = {(void *)&la, (void *)&r.bonds};
-      KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
-      count_launches(1);
-    }
-    std::swap(P, Q);  // P = q_j, Q = q_{j+1}
-  }
+  // Iterations run in chunks; after each chunk the host reads alpha and beta
+  // and stops once every sector's extreme Ritz values meet tol.
+  constexpr int kChunk = 16;
   std::vector<double> h_alpha(nab), h_beta(nab);
-  KPM_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * nab, cudaMemcpyDeviceToHost, stream));
-  KPM_CUDA(cudaMemcpyAsync(h_beta.data(), beta, sizeof(double) * nab, cudaMemcpyDeviceToHost, stream));
-  KPM_CUDA(cudaStreamSynchronize(stream));
+  std::vector<double> lo_s(n_sectors), hi_s(n_sectors), worst_s(n_sectors);
+  int done_iters = 0;
+  for (;;) {
+    const int chunk = std::min(kChunk, max_iter - done_iters);
+    for (int j = done_iters; j < done_iters + chunk; ++j) {
+      for (int mode = 1; mode <= 3; ++mode) {
+        la.P = P;
+        la.Q = Q;
+        la.mode = mode;
+        la.queue = counters + 4 * j + (mode == 1 ? 0 : (mode == 2 ? 2 : 0));
+        la.done = la.queue + 1;
+        if (mode == 3) la.queue = counters + 4 * kMaxLanczos;  // reset below
+        la.coef = mode == 1 ? beta + (size_t)j * n_sectors * 2
+                            : (mode == 2 ? alpha + (size_t)j * n_sectors * 2
+                                         : beta + (size_t)(j + 1) * n_sectors * 2);
+        la.out = mode == 1 ? alpha + (size_t)j * n_sectors * 2 : beta + (size_t)(j + 1) * n_sectors * 2;
+        if (mode == 3) KPM_CUDA(cudaMemsetAsync(la.queue, 0, sizeof(int) * 2, stream));
+        void *args[] = {(void *)&la, (void *)&r.bonds};
+        KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
+        count_launches(1);
+      }
+      std::swap(P, Q);  // P = q_j, Q = q_{j+1}
+    }
+    done_iters += chunk;
+    const size_t used = (size_t)(done_iters + 1) * n_sectors * 2;
+    KPM_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * used, cudaMemcpyDeviceToHost, stream));
+    KPM_CUDA(cudaMemcpyAsync(h_beta.data(), beta, sizeof(double) * used, cudaMemcpyDeviceToHost, stream));
+    KPM_CUDA(cudaStreamSynchronize(stream));
+    double worst_all = 0.0;
+    for (int s = 0; s < n_sectors; ++s) {
+      double lo = INFINITY, hi = -INFINITY, worst = 0.0;
+      for (int col = 0; col < 2; ++col) {
+        std::vector<double> al, be;
+        be.push_back(0.0);
+        int m = 0;
+        for (int j = 0; j < done_iters; ++j) {
+          al.push_back(h_alpha[((size_t)j * n_sectors + s) * 2 + col]);
+          ++m;
+          const double bnext = h_beta[((size_t)(j + 1) * n_sectors + s) * 2 + col];
+          if (bnext == 0.0 || m >= r.plan.dim[s]) {
+            be.push_back(0.0);
+            break;
+          }
+          be.push_back(bnext);
+        }
+        // be[i] couples i-1 and i (i >= 1); be[m] is the residual coupling
+        const double bres = be.size() > (size_t)m ? std::fabs(be[m]) : 0.0;
+        const double tmin = tridiag_eig(al, be, m, 0);
+        const double tmax = tridiag_eig(al, be, m, m - 1);
+        const double rmin = bres * ritz_last_component(al, be, m, tmin);
+        const double rmax = bres * ritz_last_component(al, be, m, tmax);
+        lo = std::min(lo, tmin - rmin);
+        hi = std::max(hi, tmax + rmax);
+        worst = std::max({worst, rmin / std::max(1.0, std::fabs(tmin)),
+                          rmax / std::max(1.0, std::fabs(tmax))});
+      }
+      lo_s[s] = lo;
+      hi_s[s] = hi;
+      worst_s[s] = worst;
+      worst_all = std::max(worst_all, worst);
+    }
+    if (worst_all <= tol || done_iters >= max_iter) break;
+  }
 
   int status = KPM_OK;
   for (int s = 0; s < n_sectors; ++s) {
-    double lo = INFINITY, hi = -INFINITY, worst = 0.0;
-    for (int col = 0; col < 2; ++col) {
-      std::vector<double> al, be;
-      be.push_back(0.0);
-      int m = 0;
-      for (int j = 0; j < max_iter; ++j) {
-        al.push_back(h_alpha[((size_t)j * n_sectors + s) * 2 + col]);
-        ++m;
-        const double bnext = h_beta[((size_t)(j + 1) * n_sectors + s) * 2 + col];
-        if (bnext == 0.0 || m >= r.plan.dim[s]) {
-          be.push_back(0.0);
-          break;
-        }
-        be.push_back(bnext);
-      }
-      // be[i] couples i-1 and i (i >= 1); be[m] is the residual coupling
-      const double bres = be.size() > (size_t)m ? std::fabs(be[m]) : 0.0;
-      const double tmin = tridiag_eig(al, be, m, 0);
-      const double tmax = tridiag_eig(al, be, m, m - 1);
-      const double rmin = bres * ritz_last_component(al, be, m, tmin);
-      const double rmax = bres * ritz_last_component(al, be, m, tmax);
-      lo = std::min(lo, tmin - rmin);
-      hi = std::max(hi, tmax + rmax);
-      worst = std::max({worst, rmin / std::max(1.0, std::fabs(tmin)),
-                        rmax / std::max(1.0, std::fabs(tmax))});
-    }
-    if (worst > tol) status = KPM_ENOTCONV;
-    double m_ = (hi - lo) / (2.0 - eps);
-    const double c_ = 0.5 * (hi + lo);
+    if (worst_s[s] > tol) status = KPM_ENOTCONV;
+    double m_ = (hi_s[s] - lo_s[s]) / (2.0 - eps);
+    const double c_ = 0.5 * (hi_s[s] + lo_s[s]);
     m_ = std::max(m_, 1e-12 * std::max(1.0, std::fabs(c_)));
     a_out[s] = m_;
     b_out[s] = c_;
-    if (e_min) e_min[s] = lo;
-    if (e_max) e_max[s] = hi;
+    if (e_min) e_min[s] = lo_s[s];
+    if (e_max) e_max[s] = hi_s[s];
   }
   if (status == KPM_ENOTCONV)
-    set_error("Lanczos residual bound above tol after %d iterations", max_iter);
+    set_error("Lanczos residual bound above tol after %d iterations", done_iters);
   return status;
 }

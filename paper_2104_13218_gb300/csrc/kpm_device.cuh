@@ -90,6 +90,17 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 
 // A 16-byte chunk of a row with the element-wise operations of the step.
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned start and size).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+// The same for an arbitrary byte range, widened to 16-byte boundaries.
+__device__ __forceinline__ void prefetch_range_l2(const void *begin, const void *end) {
+  const uintptr_t b0 = reinterpret_cast<uintptr_t>(begin) & ~uintptr_t(15);
+  const uintptr_t b1 = (reinterpret_cast<uintptr_t>(end) + 15) & ~uintptr_t(15);
+  if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const void *>(b0), (unsigned)(b1 - b0));
+}
+
 template <typename T>
 struct Chunk;
 template <>

@@ -514,6 +514,17 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
     if (t >= a.tb.n_tiles) break;
     const Tile tile = a.tb.tiles[t];
     const SectorDev sd = a.tb.sectors[tile.sector];
+    if (threadIdx.x == 0) {
+      // the tile's lists and own rows are read in order: start them towards L2 now
+      prefetch_range_l2(lists + (size_t)tile.row0 * stride, lists + ((size_t)tile.row0 + tile.count) * stride);
+      const size_t rb = (size_t)a.Rp * sizeof(T);
+      const char *xb = reinterpret_cast<const char *>(a.x) + (size_t)tile.row0 * rb;
+      prefetch_range_l2(xb, xb + tile.count * rb);
+      if (!a.first) {
+        const char *zb = reinterpret_cast<const char *>(a.zy) + (size_t)tile.row0 * rb;
+        prefetch_range_l2(zb, zb + tile.count * rb);
+      }
+    }
     if (s_sec != tile.sector) {
       __syncthreads();
       const double A = (a.first ? 1.0 : 2.0) * sd.inv_a;
