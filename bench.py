@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--lanczos-iters", type=int, default=100)
+    p.add_argument("--lanczos-tol", type=float, default=1e-6,
+                   help="relative residual bound at which the Lanczos bound estimate stops")
     return p.parse_args()
 
 
@@ -241,8 +243,8 @@ def run_ours(args):
         out = {k: torch.empty((S, w.K), dtype=torch.float64, device=dev) for k in ("mu", "mu_M", "mu_M2")}
 
         def step():
-            bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=args.lanczos_iters, tol=1e-8,
-                             seed=w.seed, workspace=ws_b)
+            bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=args.lanczos_iters,
+                             tol=args.lanczos_tol, seed=w.seed, workspace=ws_b)
             mom = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=bnd["a"], b=bnd["b"], r0=r0,
                               precision=prec, device=True, out=out, workspace=ws_m,
                               allow_ebounds=True)
@@ -318,8 +320,8 @@ def run_ours(args):
 
     # end to end through the public API with host buffers (copies inside the timed region)
     def e2e_step():
-        bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=args.lanczos_iters, tol=1e-8,
-                         seed=w.seed)
+        bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=args.lanczos_iters,
+                         tol=args.lanczos_tol, seed=w.seed)
         mom = kpm.moments(w.model, w.n_up, w.K, w.R, w.seed, a=bnd["a"], b=bnd["b"], r0=r0,
                           precision=precision, allow_ebounds=True)
         if world > 1:
@@ -345,7 +347,7 @@ def run_ours(args):
                        "chebyshev_steps_per_pass": w.steps, "eps": w.eps, "n_T": len(w.T),
                        "precision": ("fp32 vectors, fp64 reductions" if precision == "fp32"
                                      else "fp64 vectors and reductions"),
-                       "lanczos_iters": args.lanczos_iters,
+                       "lanczos_iters": args.lanczos_iters, "lanczos_tol": args.lanczos_tol,
                        "l2": f"vectors {2 * total_rows * w.R * bytes_per_unit // 3 / 1e9:.2f} GB "
                              "> 129 MB L2: inputs larger than L2, no flush",
                        "parallelism": f"replica x{world} (disjoint random vectors)"},

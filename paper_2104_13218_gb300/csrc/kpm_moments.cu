@@ -558,6 +558,8 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
       const uint32_t per = ((tile.count + kWarps - 1) / kWarps + gpw - 1) / gpw * gpw;
       const uint32_t u_begin = min(tile.count, warp * per);
       const uint32_t u_end = min(tile.count, u_begin + per);
+      // the next state's list header is loaded one state ahead
+      uint32_t hdr_next = u_begin + grp < u_end ? __ldg(lists + (size_t)(tile.row0 + u_begin + grp) * stride) : 0u;
       for (uint32_t u = u_begin + grp; u < u_end; u += gpw) {
         const int64_t row = tile.row0 + u;
         const uint32_t own = (uint32_t)row * crow + sub;
@@ -569,7 +571,8 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
           acc[c] = V{};
         }
         const uint32_t *L = lists + (size_t)row * stride;
-        const uint32_t hdr = __ldg(L);
+        const uint32_t hdr = hdr_next;
+        if (u + gpw < u_end) hdr_next = __ldg(L + (size_t)gpw * stride);
         int e = 1, tidx = 0;
         for (int g = 0; g < ng; ++g) {
           const int cnt = (hdr >> (8 * g)) & 255u;
