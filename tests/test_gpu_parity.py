@@ -390,3 +390,38 @@ def test_j1j2_square_full_space_full_size_properties():
     assert abs(s64["mu_M2"][0, 0] - 6.0) < 1e-12
     assert np.abs(s32["mu"] - s64["mu"]).max() <= TOL32
     assert np.abs(s32["mu"] - r32["mu"][:, :200]).max() == 0.0
+
+
+def test_j1j2_chain_gradient_full_size_matches_finite_differences():
+    """The gradient workload at full size: J1-J2 chain N=24, sectors M = 0..12 (M > 0
+    mirrored), R = 32, K = 1000; loss = mean squared error of chi(T) on a 50-point grid
+    in [0.1, 5] against the curve at (J1, J2) = (1.0, 0.3), evaluated at (1.0, 0.2).
+    The adjoint gradient matches central finite differences (h = 1e-5) to 1e-4."""
+    w = W.workload("j1j2chain24_grad")
+
+    def spec_at(model):
+        bnd = kpm.bounds(model, w.n_up, eps=w.eps, max_iter=120, tol=1e-8, seed=w.seed)
+        # one-state sectors get room for the finite-difference moves of J
+        return dict(model=model, n_up=w.n_up, mirror=w.mirror, a=np.maximum(bnd["a"], 0.5),
+                    b=bnd["b"], K=w.K, R=w.R, seed=w.seed, T=w.T, kernel="none", ckpt_interval=32)
+
+    with torch.no_grad():
+        target = kpm.chebyshev_thermo(torch.tensor([1.0, 0.3], dtype=torch.float64),
+                                      spec_at(w.model.with_couplings([1.0, 0.3])))[3]
+    # the gradient and the finite differences share the rescaling of (1.0, 0.2)
+    spec = spec_at(w.model)
+
+    def loss(th):
+        return ((kpm.chebyshev_thermo(th, spec)[3] - target) ** 2).mean()
+
+    theta = torch.tensor([1.0, 0.2], dtype=torch.float64, requires_grad=True)
+    loss(theta).backward()
+    h = 1e-5
+    for p in range(2):
+        tp = theta.detach().clone()
+        tm = theta.detach().clone()
+        tp[p] += h
+        tm[p] -= h
+        with torch.no_grad():
+            fd = (loss(tp).item() - loss(tm).item()) / (2 * h)
+        assert abs(theta.grad[p].item() - fd) <= 1e-4 * abs(fd), (p, theta.grad[p].item(), fd)
