@@ -102,8 +102,8 @@ int64_t kpm_sector_dim(int32_t n_sites, int32_t n_up);
  * a = (Emax - Emin)/(2 - eps) and b = (Emax + Emin)/2 (Eq. E-2-3, E-2-4)
  * and obtains extremal energies with the Lanczos method (Sec. 3.1.2).  This
  * call runs up to max_iter Lanczos steps in FP64 on the GPU for every sector
- * at once (two independent start vectors per sector with components uniform
- * in (-1, 1) from `seed`), in chunks of 16 steps, stopping after the first
+ * at once (one start vector per sector with components uniform in (-1, 1)
+ * from `seed`), in chunks of 16 steps, stopping after the first
  * chunk at which every extreme Ritz value's residual bound is within tol
  * (relative to max(1, |E|)); it widens the extreme Ritz values by their
  * residual bounds and returns per sector (host arrays of n_sectors entries):

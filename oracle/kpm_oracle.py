@@ -397,16 +397,19 @@ def thermo_from_runs(n_sites, n_up, runs, a, b, T, n_quad=0, kernel="none", mirr
     return thermo(mu, mu1, mu2, dims, mult, a, b, T, n_quad, kernel, torch_mod)
 
 
-def thermo_exact(n_sites, bi, bj, J, T, n_up=None, mirror=None):
-    """Exact Z, E, C, chi from the sector spectra (Eq. E-2-2, E-2-2-B, E-2-2-C)."""
+def thermo_exact(n_sites, bi, bj, J, T, n_up=None, mirror=None, field=0.0):
+    """Exact Z, E, C, chi from the sector spectra (Eq. E-2-2, E-2-2-B, E-2-2-C).
+
+    `field` is h = g mu_B B of the Zeeman term h sum_i s^z_i (Eq. E-3-1-1),
+    which adds h M to the energies of the sector with magnetisation M."""
     if n_up is None:
         n_up = list(range(n_sites + 1))
     T = np.asarray(T, dtype=np.float64)
     beta = 1.0 / T
     specs = []
     for i, k in enumerate(n_up):
-        e = eigenvalues(n_sites, bi, bj, J, k)
         M = k - n_sites / 2.0
+        e = eigenvalues(n_sites, bi, bj, J, k) + field * M
         mir = bool(mirror[i]) if mirror is not None else False
         specs.append((e, 2.0 if mir else 1.0, 0.0 if mir else M, M * M))
     e_ref = min(float(s[0].min()) for s in specs)

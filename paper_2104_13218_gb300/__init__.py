@@ -4,6 +4,7 @@ The compute path is libkpm.so (CUDA for sm_103a, C ABI in include/kpm.h);
 this package only marshals arguments (see api.py).
 """
 from ._lib import KPMError, lib, library_path  # noqa: F401
+from . import analysis  # noqa: F401
 from .api import (ChebyshevThermo, CModel, SectorSet, bounds, bounds_workspace_size,  # noqa: F401
                   chebyshev_thermo, moments, moments_backward, moments_backward_workspace_size,
                   moments_workspace_size, sector_dims, sector_set, thermo, thermo_backward)

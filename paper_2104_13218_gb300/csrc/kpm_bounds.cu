@@ -1,9 +1,9 @@
 // Spectral bounds of every sector for the rescaling of Eq. E-2-3 / E-2-4,
 // from the Lanczos method the paper uses for extremal energies (Sec. 3.1.2).
 //
-// All sectors run together: two independent Lanczos sequences per sector
-// (start vectors drawn like the moment vectors) stored as 2-value rows
-// (16 bytes per state) in the same stacked layout as the moment loop.  Each
+// All sectors run together: one Lanczos sequence per sector, its vectors
+// stored as 2-value rows (16 bytes per state, the second value unused) in the
+// same stacked layout as the moment loop.  Each
 // iteration is three kernels:
 //   w = H q_j - beta_j q_{j-1}  (written over q_{j-1}),  alpha_j = <w, q_j>
 //   w -= alpha_j q_j,  beta_{j+1} = |w|
@@ -23,6 +23,10 @@
 namespace kpm {
 
 constexpr int kMaxLanczos = 1000;
+// Lanczos sequences per sector: one, from a start vector with components
+// uniform in (-1, 1) (such a vector is orthogonal to no eigenvector with
+// probability one).  Rows keep two values so that they are 16 bytes wide.
+constexpr int kLanczosColumns = 1;
 
 struct LanczosArgs {
   double2 *P;        // q_{j-1} in, w out (kernel 1); w (kernel 2, 3)
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(kThreads)
     if (t >= a.tb.n_tiles) break;
     const Tile tile = a.tb.tiles[t];
     const SectorDev sd = a.tb.sectors[tile.sector];
-    const double c0 = a.coef[tile.sector * 2], c1 = a.coef[tile.sector * 2 + 1];
+    const double c0 = a.coef[tile.sector * 2];
     double acc[2] = {0.0, 0.0};
     uint32_t hb = tile.b_first;
     // one state per thread, consecutive states on consecutive lanes
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(kThreads)
         else
           s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
         double d = bd.J_quarter_sum;
-        double h0 = 0.0, h1 = 0.0;
+        double h0 = 0.0;
         for (int b = 0; b < bd.n_bonds; ++b) {
           const uint64_t m = bd.mask[b];
           const uint64_t tt = s & m;
@@ -69,32 +73,22 @@ __global__ void __launch_bounds__(kThreads)
             d -= 0.5 * bd.J[b];
             const uint64_t f = s ^ m;
             const int64_t nr = sd.row0 + (sd.n_up < 0 ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
-            const double2 v = __ldg(a.Q + nr);
-            h0 = fma(0.5 * bd.J[b], v.x, h0);
-            h1 = fma(0.5 * bd.J[b], v.y, h1);
+            h0 = fma(0.5 * bd.J[b], __ldg(&a.Q[nr].x), h0);
           }
         }
-        const double2 q = a.Q[row];
-        const double2 z = a.P[row];
-        double2 w;
-        w.x = fma(d, q.x, h0) - c0 * z.x;
-        w.y = fma(d, q.y, h1) - c1 * z.y;
-        a.P[row] = w;
-        acc[0] = fma(w.x, q.x, acc[0]);
-        acc[1] = fma(w.y, q.y, acc[1]);
+        const double q = a.Q[row].x;
+        const double z = a.P[row].x;
+        const double w = fma(d, q, h0) - c0 * z;
+        a.P[row].x = w;
+        acc[0] = fma(w, q, acc[0]);
       } else if (a.mode == 2) {
-        const double2 q = a.Q[row];
-        double2 w = a.P[row];
-        w.x -= c0 * q.x;
-        w.y -= c1 * q.y;
-        a.P[row] = w;
-        acc[0] = fma(w.x, w.x, acc[0]);
-        acc[1] = fma(w.y, w.y, acc[1]);
+        const double q = a.Q[row].x;
+        const double w = a.P[row].x - c0 * q;
+        a.P[row].x = w;
+        acc[0] = fma(w, w, acc[0]);
       } else {
-        double2 w = a.P[row];
-        w.x = c0 > 0.0 ? w.x / c0 : 0.0;
-        w.y = c1 > 0.0 ? w.y / c1 : 0.0;
-        a.P[row] = w;
+        const double w = a.P[row].x;
+        a.P[row].x = c0 > 0.0 ? w / c0 : 0.0;
       }
     }
     block_sum<2>(acc, s_red);
@@ -334,7 +328,7 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
     double worst_all = 0.0;
     for (int s = 0; s < n_sectors; ++s) {
       double lo = INFINITY, hi = -INFINITY, worst = 0.0;
-      for (int col = 0; col < 2; ++col) {
+      for (int col = 0; col < kLanczosColumns; ++col) {
         std::vector<double> al, be;
         be.push_back(0.0);
         int m = 0;

@@ -425,3 +425,48 @@ def test_j1j2_chain_gradient_full_size_matches_finite_differences():
         with torch.no_grad():
             fd = (loss(tp).item() - loss(tm).item()) / (2 * h)
         assert abs(theta.grad[p].item() - fd) <= 1e-4 * abs(fd), (p, theta.grad[p].item(), fd)
+
+
+def test_zeeman_field_by_shifted_rescaling_matches_ed():
+    """A Zeeman field h enters sector M as b -> b + h M (analysis.zeeman_shift): the GPU
+    thermodynamics of the ring N=10 with complete-basis-converged moments (large R) follows
+    the exact field-dependent curve within the statistical error."""
+    from paper_2104_13218_gb300 import analysis
+    model = W.ring(10)
+    bi, bj, J = model.arrays()
+    n_up = W.all_sectors(10)
+    h = 0.4
+    a, b = _exact_bounds(model, n_up, 0.025)
+    # the same moments serve every field: only b moves
+    mom = kpm.moments(model, n_up, 400, 200, 3, a=a, b=b)
+    T = W.log_grid(0.5, 5.0, 20)
+    bh = analysis.zeeman_shift(b, n_up, 10, h)
+    secs = kpm.sector_set(10, n_up, a, bh)
+    got = kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, T)
+    ref_kpm = O.thermo_from_runs(10, n_up, [{"mu": m} for m in mom["mu"]], a, bh, T)
+    ed = O.thermo_exact(10, bi, bj, J, T, field=h)
+    for q in ("lnZ", "E", "C", "chi"):
+        # the quadrature of the same moments: parity with the oracle
+        assert np.max(np.abs(got[q] - ref_kpm[q]) / np.maximum(1, np.abs(ref_kpm[q]))) < 1e-9, q
+        # and the physics: within the stochastic error of R = 200 vectors per sector
+        assert np.max(np.abs(got[q] - ed[q]) / np.maximum(1, np.abs(ed[q]))) < 0.05, q
+
+
+def test_realisation_statistics():
+    """P realisations (Eq. E-3-1..E-3-3): their mean approaches the exact curve with a
+    spread that shrinks like 1/sqrt(R)."""
+    from paper_2104_13218_gb300 import analysis
+    model = W.ring(10)
+    bi, bj, J = model.arrays()
+    n_up = W.all_sectors(10)
+    a, b = _exact_bounds(model, n_up, 0.025)
+    T = W.log_grid(0.5, 5.0, 10)
+    ed = O.thermo_exact(10, bi, bj, J, T)
+    r4 = analysis.realisations(model, n_up, 200, 4, 12, 5, a, b, T, exact=ed)
+    r16 = analysis.realisations(model, n_up, 200, 16, 12, 5, a, b, T, exact=ed)
+    # spread shrinks with R (dO ~ 1/sqrt(R): a factor 2 from R = 4 to 16, checked loosely)
+    assert np.mean(np.sqrt(r16["C"]["var"])) < 0.8 * np.mean(np.sqrt(r4["C"]["var"]))
+    # the mean is consistent with the exact curve within a few standard errors
+    sem = np.sqrt(r16["C"]["var"] / 12) + 1e-3
+    assert np.all(r16["C"]["dev"] < 6 * sem + 0.02)
+    assert r4["C"]["all"].shape == (12, len(T))

@@ -354,3 +354,29 @@ def test_hellmann_feynman_with_complete_basis():
     hp = O.bond_expectation_exact(8, bi, bj, J, cls, T)
     hf = -hp / T[None, :]
     assert np.max(np.abs(grads - hf) / np.abs(hf)) < 1e-8
+
+
+def test_zeeman_field_in_exact_thermo():
+    """With a field h the exact thermodynamics equals that of the dense matrix
+    H + h sum_i s^z_i built directly (the Zeeman term of Eq. E-3-1-1 is diagonal on
+    S^z bitstrings), including chi = beta (<M^2> - <M>^2) with <M> != 0."""
+    model = W.ring(6)
+    bi, bj, J = model.arrays()
+    h = 0.37
+    st = O.sector_states(6, -1)
+    M = O.magnetisation(st, 6)
+    Hd = O.dense_hamiltonian(6, bi, bj, J, st) + np.diag(h * M)
+    e, U = np.linalg.eigh(Hd)
+    Mk = np.einsum("ik,i,ik->k", U, M, U)
+    M2k = np.einsum("ik,i,ik->k", U, M * M, U)
+    T = np.array([0.3, 1.0, 3.0])
+    ex = O.thermo_exact(6, bi, bj, J, T, field=h)
+    beta = 1.0 / T
+    w = np.exp(-np.outer(beta, e - e.min()))
+    Z = w.sum(1)
+    assert np.allclose(ex["lnZ"], np.log(Z) - beta * e.min(), atol=1e-12)
+    Em = (w * e).sum(1) / Z
+    assert np.allclose(ex["E"], Em, atol=1e-12)
+    chi = beta * ((w * M2k).sum(1) / Z - ((w * Mk).sum(1) / Z) ** 2)
+    assert np.allclose(ex["chi"], chi, atol=1e-12)
+    assert np.all(np.abs((w * Mk).sum(1) / Z) > 1e-3)  # the field polarises
