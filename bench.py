@@ -297,7 +297,7 @@ def run_ours(args):
     traffic = committed_traffic(w.key, precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
-                "kernel": "cheb_step_kernel", "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "kernel": step_kernel_name(w, precision), "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": prof[1]}
 
@@ -371,6 +371,25 @@ def ctypes_read(L):
     kl = ctypes.c_int64(0)
     L.kpm_profile_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(kl))
     return ms.value, n.value, kl.value
+
+
+def step_kernel_name(w, precision):
+    """Which step kernel the library picks for this workload: the neighbour-list
+    kernel for cooperative row layouts (2+ lanes per state, 1 or 2 chunks per
+    lane) with at most 4 distinct couplings, 255 bonds and a diagonal table of
+    at most 4096 entries; the matrix-free kernel otherwise."""
+    vw = 4 if precision == "fp32" else 2
+    chunks = -(-w.R // vw)
+    cpl = -(-chunks // 32)
+    cpl = 8 if cpl > 4 else cpl
+    G = -(-chunks // cpl)
+    vals = sorted(set(w.model.J))
+    table = 1
+    for v in vals:
+        table *= sum(1 for J in w.model.J if J == v) + 1
+    grouped = len(vals) <= 4 and table <= 4096 and w.model.n_bonds > 0
+    lists = G >= 2 and cpl <= 2 and grouped and w.model.n_bonds <= 255
+    return "cheb_step_list_kernel" if lists else "cheb_step_kernel"
 
 
 def mean_flips(w):

@@ -49,7 +49,8 @@ void clear_error();
   } while (0)
 
 // ---------------------------------------------------------------- plan
-// A tile is a run of consecutive ranks of one sector, processed by one block.
+// A tile is a run of consecutive ranks of one sector, processed by one block
+// (by one warp in the neighbour-list step kernel).
 struct Tile {
   int64_t row0;      // global row (over all sectors) of the first state
   uint32_t rank0;    // rank of the first state inside its sector
@@ -103,6 +104,14 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
                Plan *plan);
 // States per tile for a layout with gpw states per warp and total_rows rows.
 int64_t choose_tile_states(int gpw, int64_t total_rows);
+// States per tile of the list kernel, whose tiles are taken by single warps.
+#ifndef KPM_LIST_TILE_STATES
+#define KPM_LIST_TILE_STATES 16
+#endif
+#ifndef KPM_LIST_MAX_TILES
+#define KPM_LIST_MAX_TILES (1 << 22)
+#endif
+int64_t list_tile_states(int gpw, int64_t total_rows);
 
 // Device copies of the plan's tables (pointers into a workspace).
 struct TablesDev {

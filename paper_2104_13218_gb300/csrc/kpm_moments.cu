@@ -35,6 +35,10 @@ struct StepArgs {
   int *done;
   int Rp, G, gpw, first;
   double half_n;    // N/2
+  // list kernel only: the previous step's tile slot and its sums ([n_sectors][NQ]),
+  // reduced at the start of this step (NULL on the first step)
+  const double *prev_partials;
+  double *prev_sums;
 };
 
 constexpr int kGB = 4;  // neighbour rows gathered per batch in the cooperative path
@@ -479,42 +483,76 @@ __global__ void __launch_bounds__(kThreads)
 #define KPM_LIST_BATCH_F64 4
 #endif
 
+// out[sec][q] = sum over the sector's tiles, in tile order per thread and then
+// over the block, of the per-tile sums ts[t][q].  Called by a whole block.
+template <int NQ>
+__device__ void reduce_sector_tiles(const double *ts, const TablesDev &tb, int sec, double *out,
+                                    double *s_red) {
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+  for (int t = tb.tile_begin[sec] + threadIdx.x; t < tb.tile_end[sec]; t += kThreads) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] += __ldcg(ts + (int64_t)t * NQ + q);
+  }
+  block_sum<NQ>(v, s_red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[(size_t)sec * NQ + q] = v[q];
+  }
+}
+
+// Coefficients of H' for the list kernel, per sector and per kind of step
+// (first: A = 1/a, later: A = 2/a), computed on the host once per run:
+// the diagonal A (d - b) for every combination of flip counts (table_size
+// entries) and A J_g / 2 for every coupling group, each as hi (+ lo in FP32).
+struct CoefDev {
+  const void *diag_hi, *diag_lo;  // [n_sectors][2][table_size] of T
+  const void *grp_hi, *grp_lo;    // [n_sectors][2][kMaxGroups] of T
+};
+
 // One Chebyshev step driven by the neighbour lists (cooperative layouts with
-// grouped couplings).  The G lanes of a state read the same list words (one
-// broadcast load each) and gather their own chunks of the listed rows.
+// grouped couplings).  Warps work independently: each takes small tiles from
+// the step's queue and writes the tile's dot products to the tile's own slot
+// of this step, so the loop has no block-wide barriers.  The slots of the
+// previous step are summed per sector, in tile order, at the start of the
+// next step (and for the last step by reduce_tile_sums_kernel).  The G lanes
+// of a state read the same list words (broadcast loads) and gather their own
+// chunks of the listed rows.
 template <typename T, int CPL, bool FULL>
 __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
     cheb_step_list_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd,
-                          const uint32_t *__restrict__ lists, int stride) {
+                          const uint32_t *__restrict__ lists, int stride, CoefDev cf) {
   using C = Chunk<T>;
   using V = typename C::type;
   constexpr int NQ = FULL ? 6 : 2;
   constexpr bool PAIR = sizeof(T) == 4;
-  extern __shared__ __align__(16) unsigned char s_dyn[];
-  T *s_dh = reinterpret_cast<T *>(s_dyn);
-  T *s_dl = s_dh + bd.table_size;
-  __shared__ T s_gh[kMaxGroups], s_gl[kMaxGroups];
-  __shared__ double s_red[kWarps * NQ];
-  __shared__ int s_tile, s_last, s_sec;
-
   const V *__restrict__ x = reinterpret_cast<const V *>(a.x);
   V *__restrict__ zy = reinterpret_cast<V *>(a.zy);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int G = a.G, gpw = a.gpw;
   const int grp = lane / G, sub = lane - grp * G;
   const bool active = grp < gpw;
   const uint32_t crow = (uint32_t)(a.Rp / C::W);
   const int ng = bd.n_groups;
-  if (threadIdx.x == 0) s_sec = -1;
-
+  const int kind = a.first ? 0 : 1;
+  const T *dh_all = reinterpret_cast<const T *>(cf.diag_hi);
+  const T *dl_all = reinterpret_cast<const T *>(cf.diag_lo);
+  const T *gh_all = reinterpret_cast<const T *>(cf.grp_hi);
+  const T *gl_all = reinterpret_cast<const T *>(cf.grp_lo);
+  if (a.prev_sums != nullptr) {
+    __shared__ double s_red[kWarps * NQ];
+    for (int sec = blockIdx.x; sec < a.tb.n_sectors; sec += gridDim.x)
+      reduce_sector_tiles<NQ>(a.prev_partials, a.tb, sec, a.prev_sums, s_red);
+  }
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int t = s_tile;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(a.queue, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= a.tb.n_tiles) break;
     const Tile tile = a.tb.tiles[t];
     const SectorDev sd = a.tb.sectors[tile.sector];
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       // the tile's lists and own rows are read in order: start them towards L2 now
       prefetch_range_l2(lists + (size_t)tile.row0 * stride, lists + ((size_t)tile.row0 + tile.count) * stride);
       const size_t rb = (size_t)a.Rp * sizeof(T);
@@ -525,42 +563,24 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
         prefetch_range_l2(zb, zb + tile.count * rb);
       }
     }
-    if (s_sec != tile.sector) {
-      __syncthreads();
-      const double A = (a.first ? 1.0 : 2.0) * sd.inv_a;
-      if (threadIdx.x < ng) {
-        const double c = A * 0.5 * bd.gJ[threadIdx.x];
-        const T hi = (T)c;
-        s_gh[threadIdx.x] = hi;
-        s_gl[threadIdx.x] = PAIR ? (T)(c - (double)hi) : (T)0;
-      }
-      for (int idx = threadIdx.x; idx < bd.table_size; idx += kThreads) {
-        double d = bd.J_quarter_sum;
-        for (int g = 0; g < ng; ++g) {
-          const int size = bd.gstart[g + 1] - bd.gstart[g];
-          d -= ((idx / bd.tstride[g]) % (size + 1)) * (0.5 * bd.gJ[g]);
-        }
-        const double ad = A * (d - sd.b);
-        const T hi = (T)ad;
-        s_dh[idx] = hi;
-        if (PAIR) s_dl[idx] = (T)(ad - (double)hi);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_sec = tile.sector;
+    const size_t cbase = (size_t)tile.sector * 2 + kind;
+    const T *dh = dh_all + cbase * bd.table_size;
+    const T *dl = dl_all + cbase * bd.table_size;
+    T gh[kMaxGroups], gl[kMaxGroups];
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) {
+      gh[g] = g < ng ? __ldg(gh_all + cbase * kMaxGroups + g) : (T)0;
+      gl[g] = (PAIR && g < ng) ? __ldg(gl_all + cbase * kMaxGroups + g) : (T)0;
     }
-    __syncthreads();
 
     double acc64[NQ];
     KahanF accf[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc64[q] = 0.0;
     if (active) {
-      const uint32_t per = ((tile.count + kWarps - 1) / kWarps + gpw - 1) / gpw * gpw;
-      const uint32_t u_begin = min(tile.count, warp * per);
-      const uint32_t u_end = min(tile.count, u_begin + per);
       // the next state's list header is loaded one state ahead
-      uint32_t hdr_next = u_begin + grp < u_end ? __ldg(lists + (size_t)(tile.row0 + u_begin + grp) * stride) : 0u;
-      for (uint32_t u = u_begin + grp; u < u_end; u += gpw) {
+      uint32_t hdr_next = grp < (int)tile.count ? __ldg(lists + (size_t)(tile.row0 + grp) * stride) : 0u;
+      for (uint32_t u = grp; u < tile.count; u += gpw) {
         const int64_t row = tile.row0 + u;
         const uint32_t own = (uint32_t)row * crow + sub;
         V xv[CPL], zv[CPL], acc[CPL];
@@ -572,41 +592,48 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
         }
         const uint32_t *L = lists + (size_t)row * stride;
         const uint32_t hdr = hdr_next;
-        if (u + gpw < u_end) hdr_next = __ldg(L + (size_t)gpw * stride);
-        int e = 1, tidx = 0;
-        for (int g = 0; g < ng; ++g) {
-          const int cnt = (hdr >> (8 * g)) & 255u;
-          tidx += cnt * bd.tstride[g];
-          V gs[CPL];
+        if (u + gpw < tile.count) hdr_next = __ldg(L + (size_t)gpw * stride);
+        // diagonal of this state: the table entry for its flip counts, loaded
+        // before the gathers so that its latency is hidden behind them
+        int tidx = 0;
 #pragma unroll
-          for (int c = 0; c < CPL; ++c) gs[c] = V{};
-          constexpr int B = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
-          for (int i = 0; i < cnt; i += B) {
-            uint32_t ci[B];
+        for (int g = 0; g < kMaxGroups; ++g)
+          if (g < ng) tidx += (int)((hdr >> (8 * g)) & 255u) * bd.tstride[g];
+        const T ad_hi = __ldg(dh + tidx);
+        const T ad_lo = PAIR ? __ldg(dl + tidx) : (T)0;
+        int e = 1;
 #pragma unroll
-            for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? __ldg(L + e + i + q) : 0u;
-            V v[B][CPL];
+        for (int g = 0; g < kMaxGroups; ++g) {
+          if (g < ng) {
+            const int cnt = (hdr >> (8 * g)) & 255u;
+            V gs[CPL];
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
+            for (int c = 0; c < CPL; ++c) gs[c] = V{};
+            constexpr int B = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
+            for (int i = 0; i < cnt; i += B) {
+              uint32_t ci[B];
 #pragma unroll
-              for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+              for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? __ldg(L + e + i + q) : 0u;
+              V v[B][CPL];
+#pragma unroll
+              for (int q = 0; q < B; ++q) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+              }
+#pragma unroll
+              for (int q = 0; q < B; ++q) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+              }
             }
+            e += cnt;
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-#pragma unroll
-              for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+            for (int c = 0; c < CPL; ++c) {
+              acc[c] = C::fma(gh[g], gs[c], acc[c]);
+              if (PAIR) acc[c] = C::fma(gl[g], gs[c], acc[c]);
             }
-          }
-          e += cnt;
-          const T gh = s_gh[g], gl = s_gl[g];
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            acc[c] = C::fma(gh, gs[c], acc[c]);
-            if (PAIR) acc[c] = C::fma(gl, gs[c], acc[c]);
           }
         }
-        const T ad_hi = s_dh[tidx];
-        const T ad_lo = PAIR ? s_dl[tidx] : (T)0;
         using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
         P2 paa{}, pba{};
 #pragma unroll
@@ -646,36 +673,21 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
 #pragma unroll
       for (int q = 0; q < NQ; ++q) acc64[q] = accf[q].value();
     }
-    block_sum<NQ>(acc64, s_red);
-    if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc64[q] = warp_sum(acc64[q]);
+    if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) a.partials[(int64_t)t * NQ + q] = acc64[q];
     }
   }
+}
 
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    for (int sec = warp; sec < a.tb.n_sectors; sec += kWarps) {
-      const int t0 = a.tb.tile_begin[sec], t1 = a.tb.tile_end[sec];
-      double v[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-      for (int tt = t0 + lane; tt < t1; tt += 32) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) v[q] += __ldcg(a.partials + (int64_t)tt * NQ + q);
-      }
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) a.sums[sec * NQ + q] = v[q];
-      }
-    }
-  }
+// Sums of the list kernel's last step: one block per sector.
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) reduce_tile_sums_kernel(const double *ts, TablesDev tb,
+                                                                    double *sums) {
+  __shared__ double s_red[kWarps * NQ];
+  reduce_sector_tiles<NQ>(ts, tb, blockIdx.x, sums, s_red);
 }
 
 // ---------------------------------------------------------------- random vectors
@@ -836,7 +848,8 @@ void *pick_step(int precision, int cpl, bool full) {
 
 size_t step_smem(const MomentsRun &r) {
   // diagonal table: hi + lo floats (FP32) or one double (FP64) per entry
-  return (size_t)r.bonds.table_size * 8;
+  // (the list kernel reads its coefficients from global memory)
+  return r.list_stride > 0 ? 0 : (size_t)r.bonds.table_size * 8;
 }
 
 int sm_count() {
@@ -867,11 +880,6 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
     rows += kpm_sector_dim(m->n_sites, n_up[s]);
     full |= n_up[s] < 0;
   }
-  KPM_TRY(build_plan(m, n_sectors, n_up, choose_tile_states(run->lay.gpw, rows), &run->plan));
-  run->NQ = run->plan.any_full ? 6 : 2;
-  KPM_REQUIRE((uint64_t)run->plan.total_rows * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
-              KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
-              (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
   fill_bonds(m, &run->bonds);
   fill_pass_masks(&run->bonds, run->lay.G);
   // neighbour lists for cooperative layouts with grouped couplings (CPL 1 or 2)
@@ -879,24 +887,100 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
       m->n_bonds <= 255)
     run->list_stride = m->n_bonds + 1;
+  const int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
+                                          : choose_tile_states(run->lay.gpw, rows);
+  KPM_TRY(build_plan(m, n_sectors, n_up, ts, &run->plan));
+  run->NQ = run->plan.any_full ? 6 : 2;
+  KPM_REQUIRE((uint64_t)run->plan.total_rows * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
+              KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
+              (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
   run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);
   (void)full;
   return KPM_OK;
 }
 
+size_t coef_bytes(const MomentsRun &r, int which) {
+  // which: 0/1 diagonal hi/lo, 2/3 group hi/lo
+  const size_t per = which < 2 ? (size_t)r.bonds.table_size : (size_t)kMaxGroups;
+  return align256((size_t)r.plan.n_sectors * 2 * per * r.lay.elem);
+}
+
 size_t run_bytes(const MomentsRun &r) {
-  return 2 * r.vec_bytes + tables_bytes(r.plan) +
+  const bool lists = r.list_stride > 0;
+  size_t coef = 0;
+  if (lists)
+    for (int w = 0; w < 4; ++w) coef += coef_bytes(r, w);
+  return 2 * r.vec_bytes + tables_bytes(r.plan) + coef +
          align256((size_t)r.plan.total_rows * r.list_stride * sizeof(uint32_t)) +
-         align256(r.plan.tiles.size() * r.NQ * sizeof(double)) +
+         align256((lists ? 2 : 1) * r.plan.tiles.size() * r.NQ * sizeof(double)) +
          align256((size_t)r.S * r.plan.n_sectors * r.NQ * sizeof(double)) +
          align256((size_t)2 * r.S * sizeof(int)) + 256;
 }
+
+namespace {
+
+// Coefficients of H' for the list kernel: per sector and kind of step (A = 1/a
+// on the first step, 2/a later), the diagonal A (d - b) for each combination
+// of anti-aligned bond counts per group, d = sum_bonds J/4 - sum_g n_g J_g / 2,
+// and the flip amplitude A J_g / 2 of each group; each split into the nearest
+// value of the vector type plus (FP32) the rounding remainder.
+template <typename T>
+int upload_coefficients_t(MomentsRun &r, const std::vector<SectorDev> &sec, Arena &arena,
+                          cudaStream_t s) {
+  const BondsDev &bd = r.bonds;
+  const int ns = r.plan.n_sectors, ng = bd.n_groups, tsz = bd.table_size;
+  const bool pair = sizeof(T) == 4;
+  std::vector<T> dh((size_t)ns * 2 * tsz), dl(dh.size(), (T)0);
+  std::vector<T> gh((size_t)ns * 2 * kMaxGroups, (T)0), gl(gh.size(), (T)0);
+  std::vector<double> d(tsz);
+  for (int idx = 0; idx < tsz; ++idx) {
+    double v = bd.J_quarter_sum;
+    for (int g = 0; g < ng; ++g) {
+      const int size = bd.gstart[g + 1] - bd.gstart[g];
+      v -= ((idx / bd.tstride[g]) % (size + 1)) * (0.5 * bd.gJ[g]);
+    }
+    d[idx] = v;
+  }
+  for (int i = 0; i < ns; ++i)
+    for (int kind = 0; kind < 2; ++kind) {
+      const double A = (kind == 0 ? 1.0 : 2.0) * sec[i].inv_a;
+      const size_t base = (size_t)i * 2 + kind;
+      for (int idx = 0; idx < tsz; ++idx) {
+        const double ad = A * (d[idx] - sec[i].b);
+        const T hi = (T)ad;
+        dh[base * tsz + idx] = hi;
+        if (pair) dl[base * tsz + idx] = (T)(ad - (double)hi);
+      }
+      for (int g = 0; g < ng; ++g) {
+        const double c = A * 0.5 * bd.gJ[g];
+        const T hi = (T)c;
+        gh[base * kMaxGroups + g] = hi;
+        if (pair) gl[base * kMaxGroups + g] = (T)(c - (double)hi);
+      }
+    }
+  const std::vector<T> *src[4] = {&dh, &dl, &gh, &gl};
+  for (int w = 0; w < 4; ++w) {
+    r.coef[w] = arena.take<char>(coef_bytes(r, w));
+    KPM_REQUIRE(r.coef[w] != nullptr, KPM_ENOMEM, "workspace too small for the step coefficients");
+    KPM_CUDA(cudaMemcpyAsync(r.coef[w], src[w]->data(), src[w]->size() * sizeof(T),
+                             cudaMemcpyHostToDevice, s));
+  }
+  return KPM_OK;
+}
+
+int upload_coefficients(MomentsRun &r, const std::vector<SectorDev> &sec, Arena &arena,
+                        cudaStream_t s) {
+  return r.precision == KPM_FP32 ? upload_coefficients_t<float>(r, sec, arena, s)
+                                 : upload_coefficients_t<double>(r, sec, arena, s);
+}
+
+}  // namespace
 
 int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cudaStream_t s,
               const int *out_index) {
   r.vA = arena.take<char>(r.vec_bytes);
   r.vB = arena.take<char>(r.vec_bytes);
-  r.partials = arena.take<double>(std::max<size_t>(1, r.plan.tiles.size() * r.NQ));
+  r.partials = arena.take<double>(std::max<size_t>(1, (r.list_stride > 0 ? 2 : 1) * r.plan.tiles.size() * r.NQ));
   r.sums = arena.take<double>((size_t)r.S * r.plan.n_sectors * r.NQ);
   r.counters = arena.take<int>((size_t)2 * r.S);
   r.flag = arena.take<int>(1);
@@ -929,6 +1013,7 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     build_lists_kernel<<<grid, kThreads, 0, s>>>(la, r.bonds);
     KPM_CUDA(cudaGetLastError());
     count_launches(1);
+    KPM_TRY(upload_coefficients(r, sec, arena, s));
   }
   KPM_CUDA(cudaMemsetAsync(r.counters, 0, sizeof(int) * 2 * r.S, s));
   KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
@@ -977,11 +1062,23 @@ int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int ste
   a.gpw = r.lay.gpw;
   a.first = first;
   a.half_n = 0.5 * r.plan.N;
+  a.prev_partials = nullptr;
+  a.prev_sums = nullptr;
+  CoefDev cf{r.coef[0], r.coef[1], r.coef[2], r.coef[3]};
+  if (r.list_stride > 0) {
+    // alternate tile slots; the previous step's slot is reduced by this launch
+    const size_t slot = r.plan.tiles.size() * r.NQ;
+    a.partials = r.partials + (step & 1) * slot;
+    if (step > 0) {
+      a.prev_partials = r.partials + ((step - 1) & 1) * slot;
+      a.prev_sums = r.sums + (size_t)(step - 1) * r.plan.n_sectors * r.NQ;
+    }
+  }
   void *fn = pick_kernel(r);
   const uint32_t *lists = r.lists;
   int stride = r.list_stride;
   void *args_q[] = {(void *)&a, (void *)&r.bonds};
-  void *args_l[] = {(void *)&a, (void *)&r.bonds, (void *)&lists, (void *)&stride};
+  void *args_l[] = {(void *)&a, (void *)&r.bonds, (void *)&lists, (void *)&stride, (void *)&cf};
   void **args = r.list_stride > 0 ? args_l : args_q;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const bool prof = r.profile && profiling();
@@ -999,7 +1096,22 @@ int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int ste
   return KPM_OK;
 }
 
+int launch_finish(const MomentsRun &r, cudaStream_t s) {
+  if (r.list_stride == 0) return KPM_OK;
+  const int last = r.S - 1;
+  const double *ts = r.partials + (last & 1) * r.plan.tiles.size() * r.NQ;
+  double *out = r.sums + (size_t)last * r.plan.n_sectors * r.NQ;
+  if (r.NQ == 6)
+    reduce_tile_sums_kernel<6><<<r.plan.n_sectors, kThreads, 0, s>>>(ts, r.tb, out);
+  else
+    reduce_tile_sums_kernel<2><<<r.plan.n_sectors, kThreads, 0, s>>>(ts, r.tb, out);
+  KPM_CUDA(cudaGetLastError());
+  count_launches(1);
+  return KPM_OK;
+}
+
 int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2, cudaStream_t s) {
+  KPM_TRY(launch_finish(r, s));
   AssembleArgs a;
   a.sums = r.sums;
   a.sectors = r.tb.sectors;

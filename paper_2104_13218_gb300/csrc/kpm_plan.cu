@@ -70,6 +70,15 @@ int64_t choose_tile_states(int gpw, int64_t total_rows) {
   return std::max<int64_t>(1, std::min(big, small));
 }
 
+int64_t list_tile_states(int gpw, int64_t total_rows) {
+  // Small warp tiles keep the states being worked on at any moment (about one
+  // tile per resident warp) close together, so that their neighbours' rows
+  // are shared in L2; tiles are enlarged only to stay within the tile limit.
+  int64_t t = std::max<int64_t>(KPM_LIST_TILE_STATES, gpw);
+  t = std::max<int64_t>(t, (total_rows + KPM_LIST_MAX_TILES - 1) / KPM_LIST_MAX_TILES);
+  return (t + gpw - 1) / gpw * gpw;
+}
+
 int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t tile_states,
                Plan *p) {
   KPM_TRY(validate_model(m));

@@ -17,7 +17,7 @@ struct MomentsRun {
   int grid = 0;            // persistent grid of the step kernel
   size_t vec_bytes = 0;    // one interleaved vector (all sectors)
   void *vA = nullptr, *vB = nullptr;
-  double *partials = nullptr;  // [n_tiles][NQ]
+  double *partials = nullptr;  // [n_tiles][NQ] ([2][n_tiles][NQ] with lists)
   double *sums = nullptr;      // [S][n_sectors][NQ]
   int *counters = nullptr;     // [2*S]: tile queue and finished-block count per step
   int *flag = nullptr;         // EBOUNDS flag
@@ -28,6 +28,10 @@ struct MomentsRun {
   // each bit-flipped neighbour's row, group by group.  Built once per run.
   int list_stride = 0;         // 0: no lists (the step works matrix-free)
   uint32_t *lists = nullptr;
+  // With lists: coefficients of H' per sector and kind of step (first, later),
+  // diagonal table hi / lo and group couplings hi / lo (lo only in FP32), and
+  // two slots of per-tile sums (partials) used by alternate steps.
+  void *coef[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // The FP32 form stores sectors smaller than this in FP64: in a tiny sector the
