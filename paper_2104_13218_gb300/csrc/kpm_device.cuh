@@ -91,6 +91,17 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 
 // A 16-byte chunk of a row with the element-wise operations of the step.
 // Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned start and size).
+// 4-byte asynchronous copy global -> shared (through L1), and its group fences.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }

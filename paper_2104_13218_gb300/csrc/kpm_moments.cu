@@ -474,8 +474,9 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Neighbour rows gathered per batch in the list kernel (FP32 / FP64 rows):
-// measured on the benchmark workloads, 8 suits FP32 and 4 suits FP64.
+// 16-byte chunks gathered per lane and batch in the list kernel (FP32 / FP64
+// rows); a batch holds KPM_LIST_BATCH_* / CPL neighbour rows.  Measured on
+// the ring and J1-J2 workloads: 8 chunks suit FP32, 4 suit FP64.
 #ifndef KPM_LIST_BATCH_F32
 #define KPM_LIST_BATCH_F32 8
 #endif
@@ -502,6 +503,12 @@ __device__ void reduce_sector_tiles(const double *ts, const TablesDev &tb, int s
   }
 }
 
+// Shared memory of the list kernel: per warp two buffers of gpw lists.
+constexpr size_t kMaxListSmem = 48 * 1024;
+inline size_t list_smem_bytes(int gpw, int stride) {
+  return (size_t)kWarps * 2 * gpw * stride * sizeof(uint32_t);
+}
+
 // Coefficients of H' for the list kernel, per sector and per kind of step
 // (first: A = 1/a, later: A = 2/a), computed on the host once per run:
 // the diagonal A (d - b) for every combination of flip counts (table_size
@@ -516,9 +523,11 @@ struct CoefDev {
 // the step's queue and writes the tile's dot products to the tile's own slot
 // of this step, so the loop has no block-wide barriers.  The slots of the
 // previous step are summed per sector, in tile order, at the start of the
-// next step (and for the last step by reduce_tile_sums_kernel).  The G lanes
-// of a state read the same list words (broadcast loads) and gather their own
-// chunks of the listed rows.
+// next step (and for the last step by reduce_tile_sums_kernel).  A warp
+// copies the lists of its next gpw states into its own shared-memory buffer
+// (cp.async, double-buffered) while it works on the current ones, so the
+// neighbour indices are on chip when the gathers start; the G lanes of a
+// state gather their own chunks of the listed rows.
 template <typename T, int CPL, bool FULL>
 __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
     cheb_step_list_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd,
@@ -540,6 +549,9 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
   const T *dl_all = reinterpret_cast<const T *>(cf.diag_lo);
   const T *gh_all = reinterpret_cast<const T *>(cf.grp_hi);
   const T *gl_all = reinterpret_cast<const T *>(cf.grp_lo);
+  extern __shared__ __align__(16) uint32_t s_lists[];  // [kWarps][2][gpw * stride]
+  const int span = gpw * stride;
+  uint32_t *wbuf = s_lists + (threadIdx.x >> 5) * 2 * span;
   if (a.prev_sums != nullptr) {
     __shared__ double s_red[kWarps * NQ];
     for (int sec = blockIdx.x; sec < a.tb.n_sectors; sec += gridDim.x)
@@ -577,10 +589,26 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
     KahanF accf[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc64[q] = 0.0;
-    if (active) {
-      // the next state's list header is loaded one state ahead
-      uint32_t hdr_next = grp < (int)tile.count ? __ldg(lists + (size_t)(tile.row0 + grp) * stride) : 0u;
-      for (uint32_t u = grp; u < tile.count; u += gpw) {
+    {
+      // lists of iteration `it` (states it*gpw ..) into wbuf[it & 1]
+      const uint32_t n_iter = (tile.count + gpw - 1) / gpw;
+      auto copy_lists = [&](uint32_t it) {
+        const uint32_t s0 = it * gpw;
+        const int nw = (int)min((uint32_t)gpw, tile.count - s0) * stride;
+        const uint32_t *src = lists + (size_t)(tile.row0 + s0) * stride;
+        uint32_t *dst = wbuf + (it & 1) * span;
+        for (int w = lane; w < nw; w += 32) cp_async4(dst + w, src + w);
+      };
+      copy_lists(0);
+      cp_async_commit();
+      for (uint32_t it = 0; it < n_iter; ++it) {
+        if (it + 1 < n_iter) copy_lists(it + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const uint32_t u = it * gpw + grp;
+        const uint32_t *L = wbuf + (it & 1) * span + grp * stride;
+        if (active && u < tile.count) {
         const int64_t row = tile.row0 + u;
         const uint32_t own = (uint32_t)row * crow + sub;
         V xv[CPL], zv[CPL], acc[CPL];
@@ -590,9 +618,7 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
           zv[c] = a.first ? V{} : __ldcs(zy + own + c * G);
           acc[c] = V{};
         }
-        const uint32_t *L = lists + (size_t)row * stride;
-        const uint32_t hdr = hdr_next;
-        if (u + gpw < tile.count) hdr_next = __ldg(L + (size_t)gpw * stride);
+        const uint32_t hdr = L[0];
         // diagonal of this state: the table entry for its flip counts, loaded
         // before the gathers so that its latency is hidden behind them
         int tidx = 0;
@@ -609,11 +635,12 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
             V gs[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) gs[c] = V{};
-            constexpr int B = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
+            constexpr int BC = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
+            constexpr int B = BC / CPL > 0 ? BC / CPL : 1;
             for (int i = 0; i < cnt; i += B) {
               uint32_t ci[B];
 #pragma unroll
-              for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? __ldg(L + e + i + q) : 0u;
+              for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? L[e + i + q] : 0u;
               V v[B][CPL];
 #pragma unroll
               for (int q = 0; q < B; ++q) {
@@ -667,7 +694,10 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
             accf[5].add(M * M * pyx);
           }
         }
+        }
+        __syncwarp();  // the buffer read here is refilled by the next iteration's copy
       }
+      cp_async_wait<0>();
     }
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -847,9 +877,10 @@ void *pick_step(int precision, int cpl, bool full) {
 }
 
 size_t step_smem(const MomentsRun &r) {
-  // diagonal table: hi + lo floats (FP32) or one double (FP64) per entry
-  // (the list kernel reads its coefficients from global memory)
-  return r.list_stride > 0 ? 0 : (size_t)r.bonds.table_size * 8;
+  // matrix-free kernel: diagonal table, hi + lo floats (FP32) or one double
+  // (FP64) per entry; list kernel: two list buffers of gpw states per warp
+  if (r.list_stride > 0) return list_smem_bytes(r.lay.gpw, r.list_stride);
+  return (size_t)r.bonds.table_size * 8;
 }
 
 int sm_count() {
@@ -885,7 +916,7 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   // neighbour lists for cooperative layouts with grouped couplings (CPL 1 or 2)
   run->list_stride = 0;
   if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
-      m->n_bonds <= 255)
+      m->n_bonds <= 255 && list_smem_bytes(run->lay.gpw, m->n_bonds + 1) <= kMaxListSmem)
     run->list_stride = m->n_bonds + 1;
   const int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
                                           : choose_tile_states(run->lay.gpw, rows);
