@@ -89,8 +89,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   return f2_from(d);
 }
 
-// A 16-byte chunk of a row with the element-wise operations of the step.
-// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned start and size).
 // 4-byte asynchronous copy global -> shared (through L1), and its group fences.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -102,6 +100,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned start and size).
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
@@ -112,6 +111,7 @@ __device__ __forceinline__ void prefetch_range_l2(const void *begin, const void 
   if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const void *>(b0), (unsigned)(b1 - b0));
 }
 
+// A 16-byte chunk of a row with the element-wise operations of the step.
 template <typename T>
 struct Chunk;
 template <>

@@ -12,11 +12,13 @@
 // (and their M- and M^2-weighted forms for a full-space run) from which
 // mu_{2n} = 2<v_n|v_n> - mu_0 and mu_{2n+1} = 2<v_{n+1}|v_n> - mu_1.
 // Tiles of consecutive states are handed out by a per-step atomic queue to a
-// persistent grid; each tile's partial sums are written to its own slot and
-// the last block to finish reduces them in tile order, so results do not
-// depend on the schedule.
+// persistent grid (to blocks in the matrix-free kernel, to single warps in
+// the neighbour-list kernel); each tile's partial sums are written to its own
+// slot and reduced in tile order (by the last block to finish, or at the
+// start of the next step), so results do not depend on the schedule.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -1208,20 +1210,67 @@ int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, c
 }
 
 int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
-            cudaStream_t s) {
-  for (int part = 0; part < 2; ++part) {
-    const bool has = part == 0 ? job.has_main : job.has_side;
-    if (!has) continue;
-    MomentsRun &r = part == 0 ? job.main : job.side;
-    KPM_TRY(launch_init(r, r.vA, seed, r0, s));
-    KPM_TRY(launch_step(r, r.vA, r.vB, 1, 0, s));
-    void *x = r.vB, *zy = r.vA;
-    for (int step = 1; step < r.S; ++step) {
-      KPM_TRY(launch_step(r, x, zy, 0, step, s));
-      std::swap(x, zy);
-    }
-    KPM_TRY(launch_assemble(r, mu, mu_M, mu_M2, s));
+            cudaStream_t s, cudaStream_t side) {
+  const bool fork = side != nullptr && job.has_main && job.has_side;
+  cudaStream_t ss = fork ? side : s;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (fork) {
+    KPM_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    KPM_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    KPM_CUDA(cudaEventRecord(ev_fork, s));
+    KPM_CUDA(cudaStreamWaitEvent(ss, ev_fork, 0));
   }
+  // The two runs are independent; with a side stream their launches are
+  // interleaved so that the small FP64 run fills the main run's idle SMs.
+  MomentsRun *runs[2] = {job.has_main ? &job.main : nullptr, job.has_side ? &job.side : nullptr};
+  cudaStream_t st[2] = {s, ss};
+  void *xs[2] = {nullptr, nullptr}, *zs[2] = {nullptr, nullptr};
+  const int S = job.K / 2;
+  for (int k = 0; k < 2; ++k) {
+    if (!runs[k]) continue;
+    KPM_TRY(launch_init(*runs[k], runs[k]->vA, seed, r0, st[k]));
+    KPM_TRY(launch_step(*runs[k], runs[k]->vA, runs[k]->vB, 1, 0, st[k]));
+    xs[k] = runs[k]->vB;
+    zs[k] = runs[k]->vA;
+    if (!fork) {
+      // serial: all steps of this run, then the next run
+      for (int step = 1; step < S; ++step) {
+        KPM_TRY(launch_step(*runs[k], xs[k], zs[k], 0, step, st[k]));
+        std::swap(xs[k], zs[k]);
+      }
+      KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k]));
+    }
+  }
+  if (fork) {
+    for (int step = 1; step < S; ++step)
+      for (int k = 0; k < 2; ++k) {
+        KPM_TRY(launch_step(*runs[k], xs[k], zs[k], 0, step, st[k]));
+        std::swap(xs[k], zs[k]);
+      }
+    for (int k = 0; k < 2; ++k) KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k]));
+    KPM_CUDA(cudaEventRecord(ev_join, ss));
+    KPM_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
+    KPM_CUDA(cudaEventDestroy(ev_fork));
+    KPM_CUDA(cudaEventDestroy(ev_join));
+  }
+  return KPM_OK;
+}
+
+// A non-blocking, lowest-priority stream per device for the FP64 side run,
+// created on first use and kept until the process exits.
+int side_stream(cudaStream_t *out) {
+  static std::mutex mtx;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  KPM_CUDA(cudaGetDevice(&dev));
+  KPM_REQUIRE(dev >= 0 && dev < 64, KPM_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mtx);
+  if (streams[dev] == nullptr) {
+    int lo = 0, hi = 0;
+    KPM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    KPM_CUDA(cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, lo));
+  }
+  *out = streams[dev];
   return KPM_OK;
 }
 
@@ -1270,7 +1319,9 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
     dmuM2 = mu_M2 ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
     KPM_REQUIRE(dmu && (!mu_M || dmuM) && (!mu_M2 || dmuM2), KPM_ENOMEM, "workspace too small");
   }
-  KPM_TRY(run_job(job, seed, r0, dmu, dmuM, dmuM2, stream));
+  cudaStream_t side = nullptr;
+  if (job.has_main && job.has_side) KPM_TRY(side_stream(&side));
+  KPM_TRY(run_job(job, seed, r0, dmu, dmuM, dmuM2, stream, side));
   const size_t nbytes = (size_t)n_sectors * n_moments * sizeof(double);
   if (!on_device) {
     KPM_CUDA(cudaMemcpyAsync(mu, dmu, nbytes, cudaMemcpyDeviceToHost, stream));

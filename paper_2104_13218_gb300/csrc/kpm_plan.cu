@@ -29,12 +29,26 @@ void clear_error() { g_error[0] = '\0'; }
 
 const char *last_error() { return g_error; }
 
+namespace {
+// Pascal's triangle up to n = 64 (C(64, 32) < 2^63), built once.
+struct PascalTable {
+  int64_t c[65][65];
+  PascalTable() {
+    for (int n = 0; n <= 64; ++n) {
+      c[n][0] = 1;
+      for (int k = 1; k <= 64; ++k) c[n][k] = n == 0 ? 0 : c[n - 1][k - 1] + c[n - 1][k];
+    }
+  }
+};
+const PascalTable &pascal() {
+  static const PascalTable t;
+  return t;
+}
+}  // namespace
+
 int64_t binom(int n, int k) {
-  if (k < 0 || n < 0 || k > n) return 0;
-  if (k > n - k) k = n - k;
-  unsigned __int128 r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (unsigned)(n - k + i) / (unsigned)i;
-  return (int64_t)r;
+  if (k < 0 || n < 0 || k > n || n > 64) return 0;
+  return pascal().c[n][k];
 }
 
 int validate_model(const kpm_model *m) {
@@ -111,6 +125,7 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
 
   const int L = p->L, H = p->H;
   const uint32_t nlo = 1u << L, nhi = 1u << H;
+  const auto &C = pascal().c;  // C[n][k], n <= 64
   p->lo_rank.clear();
   p->hi_rank.clear();
   p->lo_list.clear();
@@ -126,7 +141,7 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
       uint64_t r = 0;
       int j = 0;
       for (int q = 0; q < L; ++q)
-        if ((lo >> q) & 1u) r += (uint64_t)binom(q, ++j);
+        if ((lo >> q) & 1u) r += (uint64_t)C[q][++j];
       p->lo_rank[lo] = (uint32_t)r;
       count[__builtin_popcount(lo)]++;
     }
@@ -142,7 +157,7 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
         uint64_t r = 0;
         int j = c;
         for (int q = 0; q < H; ++q)
-          if ((hi >> q) & 1u) r += (uint64_t)binom(L + q, ++j);
+          if ((hi >> q) & 1u) r += (uint64_t)C[L + q][++j];
         p->hi_rank[(size_t)c * nhi + hi] = (uint32_t)r;
       }
     // hi-blocks of every sector in increasing order of the high pattern
@@ -165,12 +180,21 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
   p->tiles.clear();
   p->tile_begin.assign(n_sectors, 0);
   p->tile_end.assign(n_sectors, 0);
+  size_t n_tiles = 0;
+  for (int s = 0; s < n_sectors; ++s) n_tiles += (size_t)((p->dim[s] + tile_states - 1) / tile_states);
+  p->tiles.reserve(n_tiles);
   for (int s = 0; s < n_sectors; ++s) {
     p->tile_begin[s] = (int32_t)p->tiles.size();
-    int32_t hb0 = p->hb_begin[s];
-    int32_t hb1 = (n_up[s] < 0) ? hb0
-                                : ((s + 1 < n_sectors) ? p->hb_begin[s + 1] : (int32_t)p->hb_hi.size());
-    // hb_begin of later sectors is set above; for the last sector use the array end
+    const int32_t hb0 = p->hb_begin[s];
+    const int32_t hb1 = (n_up[s] < 0) ? hb0
+                                      : ((s + 1 < n_sectors) ? p->hb_begin[s + 1] : (int32_t)p->hb_hi.size());
+    // hi-block holding a rank: tiles are in increasing rank order, so the
+    // block index only moves forward (hb_off increases within a sector)
+    int32_t blk = hb0;
+    auto block_of = [&](uint32_t rank) {
+      while (blk + 1 < hb1 && p->hb_off[blk + 1] <= rank) ++blk;
+      return (uint32_t)blk;
+    };
     for (int64_t r0 = 0; r0 < p->dim[s]; r0 += tile_states) {
       Tile t;
       t.row0 = p->row0[s] + r0;
@@ -180,10 +204,8 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
       t.pad = 0;
       t.b_first = t.b_last = 0;
       if (n_up[s] >= 0) {
-        auto first = p->hb_off.begin() + hb0, last = p->hb_off.begin() + hb1;
-        uint32_t a = (uint32_t)r0, z = (uint32_t)(r0 + t.count - 1);
-        t.b_first = (uint32_t)((std::upper_bound(first, last, a) - p->hb_off.begin()) - 1);
-        t.b_last = (uint32_t)((std::upper_bound(first, last, z) - p->hb_off.begin()) - 1);
+        t.b_first = block_of((uint32_t)r0);
+        t.b_last = block_of((uint32_t)(r0 + t.count - 1));
       }
       p->tiles.push_back(t);
     }

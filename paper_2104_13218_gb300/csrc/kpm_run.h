@@ -52,9 +52,12 @@ int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
                 int precision, MomentsJob *job);
 size_t job_bytes(const MomentsJob &job);
 int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, cudaStream_t s);
-// init + K/2 steps + assembly of both runs; flag_out receives the EBOUNDS flag address
+// init + K/2 steps + assembly of both runs, all on stream s, or with a side
+// stream the FP64 side run on `side` (forked from and joined back into s).
 int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
-            cudaStream_t s);
+            cudaStream_t s, cudaStream_t side = nullptr);
+// The side stream of the current device (created on first use).
+int side_stream(cudaStream_t *out);
 
 // Builds the plan and the layout; no device work.
 int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
