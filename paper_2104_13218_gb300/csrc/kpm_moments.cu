@@ -436,11 +436,35 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
 // anti-aligned bonds and the ranks of the bit-flipped neighbours are found
 // once, here, and stored as the state's neighbour list; the list step kernel
 // then reads them instead of recomputing bitstrings and ranks at every step.
+// 16-byte chunks gathered per lane and batch in the list kernel (FP32 / FP64
+// rows); a batch holds KPM_LIST_BATCH_* / CPL neighbour rows.  Measured on
+// the ring and J1-J2 workloads: 8 chunks suit FP32, 4 suit FP64.
+#ifndef KPM_LIST_BATCH_F32
+#define KPM_LIST_BATCH_F32 8
+#endif
+#ifndef KPM_LIST_BATCH_F64
+#define KPM_LIST_BATCH_F64 4
+#endif
+
+// Neighbour rows per gather batch of the list kernel.
+__host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
+  return (fp32 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64) / cpl > 0
+             ? (fp32 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64) / cpl
+             : 1;
+}
+
+// Padding unit of each group's list entries: the FP32 gather batch, 1 in FP64.
+inline int list_pad(int precision, int cpl) {
+  return precision == KPM_FP32 ? list_batch(true, cpl) : 1;
+}
+
 struct ListArgs {
   uint32_t *lists;
   TablesDev tb;
   int stride;
-  uint32_t crow;  // 16-byte chunks per row
+  uint32_t crow;        // 16-byte chunks per row
+  int batch;            // each group's entries are padded to a multiple of this
+  uint32_t zero_chunk;  // first chunk of the all-zero row after the last state
 };
 
 __global__ void __launch_bounds__(kThreads)
@@ -470,21 +494,14 @@ __global__ void __launch_bounds__(kThreads)
           }
         }
         hdr |= cnt << (8 * g);
+        // pad the group to whole gather batches with the zero row
+        for (uint32_t k = cnt; k % a.batch != 0; ++k) L[e++] = a.zero_chunk;
       }
       L[0] = hdr;
     }
   }
 }
 
-// 16-byte chunks gathered per lane and batch in the list kernel (FP32 / FP64
-// rows); a batch holds KPM_LIST_BATCH_* / CPL neighbour rows.  Measured on
-// the ring and J1-J2 workloads: 8 chunks suit FP32, 4 suit FP64.
-#ifndef KPM_LIST_BATCH_F32
-#define KPM_LIST_BATCH_F32 8
-#endif
-#ifndef KPM_LIST_BATCH_F64
-#define KPM_LIST_BATCH_F64 4
-#endif
 
 // out[sec][q] = sum over the sector's tiles, in tile order per thread and then
 // over the block, of the per-tile sums ts[t][q].  Called by a whole block.
@@ -637,25 +654,47 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
             V gs[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) gs[c] = V{};
-            constexpr int BC = sizeof(T) == 4 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64;
-            constexpr int B = BC / CPL > 0 ? BC / CPL : 1;
-            for (int i = 0; i < cnt; i += B) {
-              uint32_t ci[B];
+            constexpr int B = list_batch(sizeof(T) == 4, CPL);
+            if constexpr (sizeof(T) == 4) {
+              // FP32 lists pad each group to whole batches with the index of an
+              // all-zero row, so every batch is gathered without predicates
+              const int padded = (cnt + B - 1) / B * B;
+              for (int i = 0; i < padded; i += B) {
+                V v[B][CPL];
 #pragma unroll
-              for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? L[e + i + q] : 0u;
-              V v[B][CPL];
+                for (int q = 0; q < B; ++q) {
+                  const uint32_t ci = L[e + i + q];
 #pragma unroll
-              for (int q = 0; q < B; ++q) {
+                  for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + sub + c * G);
+                }
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+                for (int q = 0; q < B; ++q) {
+#pragma unroll
+                  for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                }
               }
+              e += padded;
+            } else {
+              // FP64 lists are unpadded: the last batch is predicated (zero-row
+              // loads of 16 lanes x 16 bytes would cost more than the predicates)
+              for (int i = 0; i < cnt; i += B) {
+                uint32_t ci[B];
 #pragma unroll
-              for (int q = 0; q < B; ++q) {
+                for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? L[e + i + q] : 0u;
+                V v[B][CPL];
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                for (int q = 0; q < B; ++q) {
+#pragma unroll
+                  for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+                }
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+#pragma unroll
+                  for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                }
               }
+              e += cnt;
             }
-            e += cnt;
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
               acc[c] = C::fma(gh[g], gs[c], acc[c]);
@@ -918,16 +957,25 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   // neighbour lists for cooperative layouts with grouped couplings (CPL 1 or 2)
   run->list_stride = 0;
   if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
-      m->n_bonds <= 255 && list_smem_bytes(run->lay.gpw, m->n_bonds + 1) <= kMaxListSmem)
-    run->list_stride = m->n_bonds + 1;
+      m->n_bonds <= 255) {
+    // header word, then each group's entries (FP32: padded to whole gather batches)
+    const int B = list_pad(precision, run->lay.cpl);
+    int stride = 1;
+    for (int g = 0; g < run->bonds.n_groups; ++g) {
+      const int size = run->bonds.gstart[g + 1] - run->bonds.gstart[g];
+      stride += (size + B - 1) / B * B;
+    }
+    if (list_smem_bytes(run->lay.gpw, stride) <= kMaxListSmem) run->list_stride = stride;
+  }
   const int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
                                           : choose_tile_states(run->lay.gpw, rows);
   KPM_TRY(build_plan(m, n_sectors, n_up, ts, &run->plan));
   run->NQ = run->plan.any_full ? 6 : 2;
-  KPM_REQUIRE((uint64_t)run->plan.total_rows * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
+  KPM_REQUIRE((uint64_t)(run->plan.total_rows + 1) * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
               KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
               (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
-  run->vec_bytes = align256((size_t)run->plan.total_rows * run->lay.Rp * run->lay.elem);
+  // one all-zero row after the last state: the padding entries of the lists point to it
+  run->vec_bytes = align256((size_t)(run->plan.total_rows + 1) * run->lay.Rp * run->lay.elem);
   (void)full;
   return KPM_OK;
 }
@@ -1042,6 +1090,11 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     la.tb = r.tb;
     la.stride = r.list_stride;
     la.crow = (uint32_t)(r.lay.Rp / r.lay.vec_width);
+    la.batch = list_pad(r.precision, r.lay.cpl);
+    la.zero_chunk = (uint32_t)r.plan.total_rows * la.crow;
+    const size_t row_bytes = (size_t)r.lay.Rp * r.lay.elem;
+    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vA) + (size_t)r.plan.total_rows * row_bytes, 0, row_bytes, s));
+    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vB) + (size_t)r.plan.total_rows * row_bytes, 0, row_bytes, s));
     const int grid = (int)std::min<int64_t>((int64_t)r.plan.tiles.size(), (int64_t)8 * sm_count());
     build_lists_kernel<<<grid, kThreads, 0, s>>>(la, r.bonds);
     KPM_CUDA(cudaGetLastError());
