@@ -522,6 +522,10 @@ __device__ void reduce_sector_tiles(const double *ts, const TablesDev &tb, int s
   }
 }
 
+// Bytes after the zero row that the list kernel's gathers may read (and
+// ignore) when a lane's last chunk slot lies past the end of a row.
+constexpr size_t kRowSlack = 32 * 16;
+
 // Shared memory of the list kernel: per warp two buffers of gpw lists.
 constexpr size_t kMaxListSmem = 48 * 1024;
 inline size_t list_smem_bytes(int gpw, int stride) {
@@ -562,6 +566,11 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
   const int grp = lane / G, sub = lane - grp * G;
   const bool active = grp < gpw;
   const uint32_t crow = (uint32_t)(a.Rp / C::W);
+  // chunk c of a lane is sub + c * G; with the two-state FP32 mapping
+  // (G = 16, CPL = 2) the last slots of a row may lie past its chunks
+  bool valid[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) valid[c] = (uint32_t)(sub + c * G) < crow;
   const int ng = bd.n_groups;
   const int kind = a.first ? 0 : 1;
   const T *dh_all = reinterpret_cast<const T *>(cf.diag_hi);
@@ -633,8 +642,8 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
         V xv[CPL], zv[CPL], acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-          xv[c] = x[own + c * G];
-          zv[c] = a.first ? V{} : __ldcs(zy + own + c * G);
+          xv[c] = valid[c] ? x[own + c * G] : V{};
+          zv[c] = (a.first || !valid[c]) ? V{} : __ldcs(zy + own + c * G);
           acc[c] = V{};
         }
         const uint32_t hdr = L[0];
@@ -709,8 +718,10 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
           V h = acc[c];
           if (PAIR) h = C::fma(ad_lo, xv[c], h);
           const V y = C::fma_sub(ad_hi, xv[c], h, zv[c]);
-          C::dots(xv[c], y, paa, pba);
-          __stcs(zy + own + c * G, y);
+          if (valid[c]) {
+            C::dots(xv[c], y, paa, pba);
+            __stcs(zy + own + c * G, y);
+          }
         }
         const T pxx = paa.x + paa.y, pyx = pba.x + pba.y;
         if constexpr (sizeof(T) == 8) {
@@ -958,6 +969,15 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   run->list_stride = 0;
   if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
       m->n_bonds <= 255) {
+    // FP32 rows of 17..32 chunks: two states per warp, 16 lanes x 2 chunks
+    // each (the row layout in memory is unchanged; lanes whose second slot
+    // lies past the row's chunks skip it), which halves the per-state work
+    // of the warp.
+    if (precision == KPM_FP32 && run->lay.cpl == 1 && run->lay.G > 16) {
+      run->lay.G = 16;
+      run->lay.cpl = 2;
+      run->lay.gpw = 2;
+    }
     // header word, then each group's entries (FP32: padded to whole gather batches)
     const int B = list_pad(precision, run->lay.cpl);
     int stride = 1;
@@ -975,7 +995,7 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
               KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
               (long long)run->plan.total_rows, run->lay.Rp / run->lay.vec_width);
   // one all-zero row after the last state: the padding entries of the lists point to it
-  run->vec_bytes = align256((size_t)(run->plan.total_rows + 1) * run->lay.Rp * run->lay.elem);
+  run->vec_bytes = align256((size_t)(run->plan.total_rows + 1) * run->lay.Rp * run->lay.elem + kRowSlack);
   (void)full;
   return KPM_OK;
 }

@@ -86,8 +86,8 @@ def test_all_sectors_ragged_in_one_launch(precision, tol):
 
 @pytest.mark.parametrize("precision,R", [("fp64", 1), ("fp64", 3), ("fp64", 20), ("fp64", 100),
                                          ("fp64", 150), ("fp64", 256), ("fp64", 300), ("fp64", 512),
-                                         ("fp32", 1), ("fp32", 4), ("fp32", 25), ("fp32", 100),
-                                         ("fp32", 260), ("fp32", 512)])
+                                         ("fp32", 1), ("fp32", 4), ("fp32", 25), ("fp32", 68),
+                                         ("fp32", 100), ("fp32", 128), ("fp32", 260), ("fp32", 512)])
 def test_row_layouts(precision, R):
     """Every lanes-per-state / chunks-per-lane layout, on a random model with mixed sectors."""
     model = W.random_bonds(12, 18, 4)
