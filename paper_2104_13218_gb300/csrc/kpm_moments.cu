@@ -436,22 +436,34 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
 // anti-aligned bonds and the ranks of the bit-flipped neighbours are found
 // once, here, and stored as the state's neighbour list; the list step kernel
 // then reads them instead of recomputing bitstrings and ranks at every step.
-// 16-byte chunks gathered per lane and batch in the list kernel (FP32 / FP64
-// rows); a batch holds KPM_LIST_BATCH_* / CPL neighbour rows.  Measured on
-// the ring and J1-J2 workloads: 8 chunks suit FP32, 4 suit FP64.
-#ifndef KPM_LIST_BATCH_F32
-#define KPM_LIST_BATCH_F32 8
+// Neighbour rows gathered per batch in the list kernel, by row type and
+// chunks per lane.  Measured on the ring (R=100: FP32 CPL 2, FP64 CPL 2) and
+// J1-J2 workloads (R=64 FP32 and R=32 FP64: CPL 1).
+#ifndef KPM_LIST_BATCH_F32_CPL1
+#define KPM_LIST_BATCH_F32_CPL1 16
+#endif
+#ifndef KPM_LIST_BATCH_F32_CPL2
+#define KPM_LIST_BATCH_F32_CPL2 4
 #endif
 #ifndef KPM_LIST_BATCH_F64
-#define KPM_LIST_BATCH_F64 4
+#define KPM_LIST_BATCH_F64 4  // chunks per lane and batch (4 rows at CPL 1, 2 at CPL 2)
 #endif
 
 // Neighbour rows per gather batch of the list kernel.
 __host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
-  return (fp32 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64) / cpl > 0
-             ? (fp32 ? KPM_LIST_BATCH_F32 : KPM_LIST_BATCH_F64) / cpl
-             : 1;
+  return fp32 ? (cpl == 1 ? KPM_LIST_BATCH_F32_CPL1 : KPM_LIST_BATCH_F32_CPL2)
+              : (KPM_LIST_BATCH_F64 / cpl > 0 ? KPM_LIST_BATCH_F64 / cpl : 1);
 }
+
+// Minimum resident blocks per SM requested for the list kernel: 4 (64
+// registers) for FP32 rows at 2 chunks per lane, 3 (80 registers) otherwise,
+// as measured on the ring and J1-J2 workloads.
+#ifndef KPM_LIST_MIN_BLOCKS_F32_CPL2
+#define KPM_LIST_MIN_BLOCKS_F32_CPL2 4
+#endif
+#ifndef KPM_LIST_MIN_BLOCKS
+#define KPM_LIST_MIN_BLOCKS 3
+#endif
 
 // Padding unit of each group's list entries: the FP32 gather batch, 1 in FP64.
 inline int list_pad(int precision, int cpl) {
@@ -552,7 +564,8 @@ struct CoefDev {
 // neighbour indices are on chip when the gathers start; the G lanes of a
 // state gather their own chunks of the listed rows.
 template <typename T, int CPL, bool FULL>
-__global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_LIST_MIN_BLOCKS_F32_CPL2
+                                                                          : KPM_LIST_MIN_BLOCKS)
     cheb_step_list_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ BondsDev bd,
                           const uint32_t *__restrict__ lists, int stride, CoefDev cf) {
   using C = Chunk<T>;
