@@ -607,7 +607,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
     const SectorDev sd = a.tb.sectors[tile.sector];
     if (lane == 0) {
       // the tile's lists and own rows are read in order: start them towards L2 now
-      prefetch_range_l2(lists + (size_t)tile.row0 * stride, lists + ((size_t)tile.row0 + tile.count) * stride);
+      prefetch_range_l2(lists + (size_t)tile.row0 * stride,
+                        lists + ((size_t)tile.row0 + tile.count) * stride);
       const size_t rb = (size_t)a.Rp * sizeof(T);
       const char *xb = reinterpret_cast<const char *>(a.x) + (size_t)tile.row0 * rb;
       prefetch_range_l2(xb, xb + tile.count * rb);
@@ -650,115 +651,116 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
         const uint32_t u = it * gpw + grp;
         const uint32_t *L = wbuf + (it & 1) * span + grp * stride;
         if (active && u < tile.count) {
-        const int64_t row = tile.row0 + u;
-        const uint32_t own = (uint32_t)row * crow + sub;
-        V xv[CPL], zv[CPL], acc[CPL];
+          const int64_t row = tile.row0 + u;
+          const uint32_t own = (uint32_t)row * crow + sub;
+          V xv[CPL], zv[CPL], acc[CPL];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          xv[c] = valid[c] ? x[own + c * G] : V{};
-          zv[c] = (a.first || !valid[c]) ? V{} : __ldcs(zy + own + c * G);
-          acc[c] = V{};
-        }
-        const uint32_t hdr = L[0];
-        // diagonal of this state: the table entry for its flip counts, loaded
-        // before the gathers so that its latency is hidden behind them
-        int tidx = 0;
+          for (int c = 0; c < CPL; ++c) {
+            xv[c] = valid[c] ? x[own + c * G] : V{};
+            zv[c] = (a.first || !valid[c]) ? V{} : __ldcs(zy + own + c * G);
+            acc[c] = V{};
+          }
+          const uint32_t hdr = L[0];
+          // diagonal of this state: the table entry for its flip counts, loaded
+          // before the gathers so that its latency is hidden behind them
+          int tidx = 0;
 #pragma unroll
-        for (int g = 0; g < kMaxGroups; ++g)
-          if (g < ng) tidx += (int)((hdr >> (8 * g)) & 255u) * bd.tstride[g];
-        const T ad_hi = __ldg(dh + tidx);
-        const T ad_lo = PAIR ? __ldg(dl + tidx) : (T)0;
-        int e = 1;
+          for (int g = 0; g < kMaxGroups; ++g)
+            if (g < ng) tidx += (int)((hdr >> (8 * g)) & 255u) * bd.tstride[g];
+          const T ad_hi = __ldg(dh + tidx);
+          const T ad_lo = PAIR ? __ldg(dl + tidx) : (T)0;
+          int e = 1;
 #pragma unroll
-        for (int g = 0; g < kMaxGroups; ++g) {
-          if (g < ng) {
-            const int cnt = (hdr >> (8 * g)) & 255u;
-            V gs[CPL];
+          for (int g = 0; g < kMaxGroups; ++g) {
+            if (g < ng) {
+              const int cnt = (hdr >> (8 * g)) & 255u;
+              V gs[CPL];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) gs[c] = V{};
-            constexpr int B = list_batch(sizeof(T) == 4, CPL);
-            if constexpr (sizeof(T) == 4) {
-              // FP32 lists pad each group to whole batches with the index of an
-              // all-zero row, so every batch is gathered without predicates
-              const int padded = (cnt + B - 1) / B * B;
-              for (int i = 0; i < padded; i += B) {
-                V v[B][CPL];
+              for (int c = 0; c < CPL; ++c) gs[c] = V{};
+              constexpr int B = list_batch(sizeof(T) == 4, CPL);
+              if constexpr (sizeof(T) == 4) {
+                // FP32 lists pad each group to whole batches with the index of an
+                // all-zero row, so every batch is gathered without predicates
+                const int padded = (cnt + B - 1) / B * B;
+                for (int i = 0; i < padded; i += B) {
+                  V v[B][CPL];
 #pragma unroll
-                for (int q = 0; q < B; ++q) {
-                  const uint32_t ci = L[e + i + q];
+                  for (int q = 0; q < B; ++q) {
+                    const uint32_t ci = L[e + i + q];
 #pragma unroll
-                  for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + sub + c * G);
+                    for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + sub + c * G);
+                  }
+#pragma unroll
+                  for (int q = 0; q < B; ++q) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                  }
                 }
+                e += padded;
+              } else {
+                // FP64 lists are unpadded: the last batch is predicated (zero-row
+                // loads of 16 lanes x 16 bytes would cost more than the predicates)
+                for (int i = 0; i < cnt; i += B) {
+                  uint32_t ci[B];
 #pragma unroll
-                for (int q = 0; q < B; ++q) {
+                  for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? L[e + i + q] : 0u;
+                  V v[B][CPL];
 #pragma unroll
-                  for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                  for (int q = 0; q < B; ++q) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+                      v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+                  }
+#pragma unroll
+                  for (int q = 0; q < B; ++q) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
+                  }
                 }
+                e += cnt;
               }
-              e += padded;
-            } else {
-              // FP64 lists are unpadded: the last batch is predicated (zero-row
-              // loads of 16 lanes x 16 bytes would cost more than the predicates)
-              for (int i = 0; i < cnt; i += B) {
-                uint32_t ci[B];
 #pragma unroll
-                for (int q = 0; q < B; ++q) ci[q] = (i + q < cnt) ? L[e + i + q] : 0u;
-                V v[B][CPL];
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-#pragma unroll
-                  for (int c = 0; c < CPL; ++c) v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
-                }
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-#pragma unroll
-                  for (int c = 0; c < CPL; ++c) gs[c] = C::add(gs[c], v[q][c]);
-                }
+              for (int c = 0; c < CPL; ++c) {
+                acc[c] = C::fma(gh[g], gs[c], acc[c]);
+                if (PAIR) acc[c] = C::fma(gl[g], gs[c], acc[c]);
               }
-              e += cnt;
-            }
-#pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-              acc[c] = C::fma(gh[g], gs[c], acc[c]);
-              if (PAIR) acc[c] = C::fma(gl[g], gs[c], acc[c]);
             }
           }
-        }
-        using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-        P2 paa{}, pba{};
+          using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+          P2 paa{}, pba{};
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          V h = acc[c];
-          if (PAIR) h = C::fma(ad_lo, xv[c], h);
-          const V y = C::fma_sub(ad_hi, xv[c], h, zv[c]);
-          if (valid[c]) {
-            C::dots(xv[c], y, paa, pba);
-            __stcs(zy + own + c * G, y);
+          for (int c = 0; c < CPL; ++c) {
+            V h = acc[c];
+            if (PAIR) h = C::fma(ad_lo, xv[c], h);
+            const V y = C::fma_sub(ad_hi, xv[c], h, zv[c]);
+            if (valid[c]) {
+              C::dots(xv[c], y, paa, pba);
+              __stcs(zy + own + c * G, y);
+            }
           }
-        }
-        const T pxx = paa.x + paa.y, pyx = pba.x + pba.y;
-        if constexpr (sizeof(T) == 8) {
-          acc64[0] += pxx;
-          acc64[1] += pyx;
-          if (FULL) {
-            const double M = sd.n_up < 0 ? (double)__popcll((uint64_t)(row - sd.row0)) - a.half_n : sd.Mval;
-            acc64[2] += M * pxx;
-            acc64[3] += M * pyx;
-            acc64[4] += M * M * pxx;
-            acc64[5] += M * M * pyx;
+          const T pxx = paa.x + paa.y, pyx = pba.x + pba.y;
+          if constexpr (sizeof(T) == 8) {
+            acc64[0] += pxx;
+            acc64[1] += pyx;
+            if (FULL) {
+              const double M = sd.n_up < 0 ? (double)__popcll((uint64_t)(row - sd.row0)) - a.half_n : sd.Mval;
+              acc64[2] += M * pxx;
+              acc64[3] += M * pyx;
+              acc64[4] += M * M * pxx;
+              acc64[5] += M * M * pyx;
+            }
+          } else {
+            accf[0].add(pxx);
+            accf[1].add(pyx);
+            if (FULL) {
+              const float M = sd.n_up < 0 ? (float)__popcll((uint64_t)(row - sd.row0)) - (float)a.half_n
+                                          : (float)sd.Mval;
+              accf[2].add(M * pxx);
+              accf[3].add(M * pyx);
+              accf[4].add(M * M * pxx);
+              accf[5].add(M * M * pyx);
+            }
           }
-        } else {
-          accf[0].add(pxx);
-          accf[1].add(pyx);
-          if (FULL) {
-            const float M = sd.n_up < 0 ? (float)__popcll((uint64_t)(row - sd.row0)) - (float)a.half_n
-                                        : (float)sd.Mval;
-            accf[2].add(M * pxx);
-            accf[3].add(M * pyx);
-            accf[4].add(M * M * pxx);
-            accf[5].add(M * M * pyx);
-          }
-        }
         }
         __syncwarp();  // the buffer read here is refilled by the next iteration's copy
       }
@@ -1094,7 +1096,8 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
               const int *out_index) {
   r.vA = arena.take<char>(r.vec_bytes);
   r.vB = arena.take<char>(r.vec_bytes);
-  r.partials = arena.take<double>(std::max<size_t>(1, (r.list_stride > 0 ? 2 : 1) * r.plan.tiles.size() * r.NQ));
+  const size_t n_partials = (r.list_stride > 0 ? 2 : 1) * r.plan.tiles.size() * r.NQ;
+  r.partials = arena.take<double>(std::max<size_t>(1, n_partials));
   r.sums = arena.take<double>((size_t)r.S * r.plan.n_sectors * r.NQ);
   r.counters = arena.take<int>((size_t)2 * r.S);
   r.flag = arena.take<int>(1);
@@ -1126,8 +1129,9 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     la.batch = list_pad(r.precision, r.lay.cpl);
     la.zero_chunk = (uint32_t)r.plan.total_rows * la.crow;
     const size_t row_bytes = (size_t)r.lay.Rp * r.lay.elem;
-    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vA) + (size_t)r.plan.total_rows * row_bytes, 0, row_bytes, s));
-    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vB) + (size_t)r.plan.total_rows * row_bytes, 0, row_bytes, s));
+    const size_t zero_off = (size_t)r.plan.total_rows * row_bytes;  // the zero row of both vectors
+    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vA) + zero_off, 0, row_bytes, s));
+    KPM_CUDA(cudaMemsetAsync(static_cast<char *>(r.vB) + zero_off, 0, row_bytes, s));
     const int grid = (int)std::min<int64_t>((int64_t)r.plan.tiles.size(), (int64_t)8 * sm_count());
     build_lists_kernel<<<grid, kThreads, 0, s>>>(la, r.bonds);
     KPM_CUDA(cudaGetLastError());
