@@ -1299,17 +1299,37 @@ int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, c
   return KPM_OK;
 }
 
+namespace {
+
+// Forks `side` from `s` and joins it back when it goes out of scope, also on
+// an early error return, so that work queued on `s` afterwards (such as the
+// release of the workspace) is ordered after everything queued on `side`.
+struct ForkJoin {
+  cudaStream_t s = nullptr, side = nullptr;
+  cudaEvent_t ev = nullptr;
+  int fork(cudaStream_t main, cudaStream_t other) {
+    KPM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    KPM_CUDA(cudaEventRecord(ev, main));
+    KPM_CUDA(cudaStreamWaitEvent(other, ev, 0));
+    s = main;
+    side = other;
+    return KPM_OK;
+  }
+  ~ForkJoin() {
+    if (ev == nullptr) return;
+    if (side != nullptr && cudaEventRecord(ev, side) == cudaSuccess) cudaStreamWaitEvent(s, ev, 0);
+    cudaEventDestroy(ev);
+  }
+};
+
+}  // namespace
+
 int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
             cudaStream_t s, cudaStream_t side) {
   const bool fork = side != nullptr && job.has_main && job.has_side;
   cudaStream_t ss = fork ? side : s;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  if (fork) {
-    KPM_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    KPM_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
-    KPM_CUDA(cudaEventRecord(ev_fork, s));
-    KPM_CUDA(cudaStreamWaitEvent(ss, ev_fork, 0));
-  }
+  ForkJoin fj;
+  if (fork) KPM_TRY(fj.fork(s, ss));
   // The two runs are independent; with a side stream their launches are
   // interleaved so that the small FP64 run fills the main run's idle SMs.
   MomentsRun *runs[2] = {job.has_main ? &job.main : nullptr, job.has_side ? &job.side : nullptr};
@@ -1338,12 +1358,8 @@ int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_
         std::swap(xs[k], zs[k]);
       }
     for (int k = 0; k < 2; ++k) KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k]));
-    KPM_CUDA(cudaEventRecord(ev_join, ss));
-    KPM_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
-    KPM_CUDA(cudaEventDestroy(ev_fork));
-    KPM_CUDA(cudaEventDestroy(ev_join));
   }
-  return KPM_OK;
+  return KPM_OK;  // fj joins the side stream into s here
 }
 
 // A non-blocking, lowest-priority stream per device for the FP64 side run,
