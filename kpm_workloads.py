@@ -103,6 +103,15 @@ def ladder(n: int, J_rung: float = 1.0, J_leg: float = 1.0) -> Model:
     return _model(f"ladder{n}", n, bonds, cls)
 
 
+def sawtooth(n: int, J1: float = -1.0, J2: float = 0.45) -> Model:
+    """Periodic sawtooth (delta) chain of n spins (Sec. 3.3): J1 (class 0) between
+    neighbours i, i+1 around the chain, J2 (class 1) between the basal sites
+    2k, 2k+2; the odd sites are the apices."""
+    bonds = [(i, (i + 1) % n, J1) for i in range(n)]
+    bonds += [(2 * k, (2 * k + 2) % n, J2) for k in range(n // 2)]
+    return _model(f"sawtooth{n}", n, bonds, [0] * n + [1] * (n // 2))
+
+
 def triangle(J: float = 1.0) -> Model:
     return _model("triangle", 3, [(0, 1, J), (1, 2, J), (0, 2, J)])
 

@@ -103,6 +103,18 @@ def test_row_layouts(precision, R):
     _check_moments(gpu, ref, n_up, model, TOL64 if precision == "fp64" else TOL32)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_sawtooth_all_sectors(precision, tol):
+    """Sawtooth chain (Sec. 3.3: ferromagnetic J1 = -1, J2 = 0.45 between basal sites),
+    N = 14, all 15 sectors, against the oracle."""
+    model = W.sawtooth(14, -1.0, 0.45)
+    n_up = list(range(15))
+    a, b = _exact_bounds(model, n_up, 0.025)
+    gpu = kpm.moments(model, n_up, 64, 20, 7, a=a, b=b, precision=precision)
+    ref = _oracle_runs(model, n_up, a, b, 64, 20, 7)
+    _check_moments(gpu, ref, n_up, model, tol)
+
+
 def test_many_tiles_and_ragged_tail():
     """A sector spanning many tiles with a ragged last tile (N = 16, k = 7: 11440 states)."""
     model = W.j1j2_chain(16, 1.0, 0.4)

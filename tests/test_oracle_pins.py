@@ -108,6 +108,24 @@ def test_ferromagnetic_state_is_top_for_af_couplings():
 
 # --------------------------------------------------------------------------- moments
 
+@pytest.mark.parametrize("n", [8, 10, 12])
+def test_sawtooth_flat_band_at_the_critical_point(n):
+    """Sawtooth chain at |J2/J1| = 1/2 with J1 < 0 (the quantum critical point of
+    Sec. 3.3): the one-magnon band is flat and degenerate with the ferromagnetic
+    state, so the sector with one flipped spin has exactly n/2 states at the
+    ferromagnetic energy sum_b J_b / 4 and a gap above them."""
+    model = W.sawtooth(n, -1.0, 0.5)
+    bi, bj, J = model.arrays()
+    assert len(J) == n + n // 2
+    e_fm = J.sum() / 4.0
+    e = np.sort(O.eigenvalues(n, bi, bj, J, n - 1))
+    assert np.allclose(e[: n // 2], e_fm, atol=1e-12)
+    assert e[n // 2] > e_fm + 0.1
+    # away from the critical point the degeneracy is lifted
+    e45 = np.sort(O.eigenvalues(n, *W.sawtooth(n, -1.0, 0.45).arrays(), n - 1))
+    assert np.sum(np.abs(e45 - e45[0]) < 1e-9) < n // 2
+
+
 def test_complete_basis_moments_equal_exact_traces():
     """With a complete orthonormal basis (R = D unit vectors) the estimator is exact (Sec. 2)."""
     m = W.random_bonds(8, 12, 3)
