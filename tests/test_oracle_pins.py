@@ -398,3 +398,37 @@ def test_zeeman_field_in_exact_thermo():
     chi = beta * ((w * M2k).sum(1) / Z - ((w * Mk).sum(1) / Z) ** 2)
     assert np.allclose(ex["chi"], chi, atol=1e-12)
     assert np.all(np.abs((w * Mk).sum(1) / Z) > 1e-3)  # the field polarises
+
+
+def test_ghost_dip_of_the_ladder_with_exact_traces():
+    """The "ghost dip" of Sec. 3.1.1: in the standard configuration (N_deg = 100,
+    eps = 0, N~ = 100, g_n = 1) the heat capacity of the AF two-leg ladder
+    deviates from exact diagonalisation at T ~ 1e-3 .. 1e-2 even with exact
+    (complete-basis) traces, so the deviation is systematic, while it agrees at
+    higher T.  Shown here for N = 14 (the paper's figure is for N = 16)."""
+    N = 14
+    model = W.ladder(N, 1.0, 1.0)
+    arr = model.arrays()
+    n_up = list(range(N // 2, N + 1))
+    mirror = [0 if k == N // 2 else 1 for k in n_up]
+    dims, mult, m1, m2 = O.sector_weights(N, n_up, mirror)
+    T = np.logspace(-3.5, 1.0, 46)
+    mu, mu1, mu2, a, b = [], [], [], [], []
+    for i, k in enumerate(n_up):
+        e = O.eigenvalues(N, *arr, k)
+        ai, bi = O.rescale(e.min(), e.max(), 0.0)
+        x = O.exact_moments(e, ai, bi, 100)
+        mu.append(x)
+        mu1.append(m1[i] * x)
+        mu2.append(m2[i] * x)
+        a.append(ai)
+        b.append(bi)
+    th = O.thermo(mu, mu1, mu2, dims, mult, np.array(a), np.array(b), T, 100, "none")
+    ex = O.thermo_exact(N, *arr, T, n_up=n_up, mirror=mirror)
+    dev = th["C"] - ex["C"]
+    low = (T >= 1e-3) & (T <= 1e-2)
+    assert dev[low].min() < -0.05                       # a dip well below the exact C ~ 0
+    t_min = T[np.argmin(dev)]
+    assert 1e-3 <= t_min <= 1e-2                        # located where the paper sees it
+    high = T >= 0.05
+    assert np.abs(dev[high]).max() < 1e-8 * np.abs(ex["C"][high]).max()
