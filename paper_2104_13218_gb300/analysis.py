@@ -11,6 +11,9 @@ and fits of the couplings to thermodynamic curves.
   moments of (H + h M - b')/a with b' = b + h M are those of (H - b)/a and
   the field enters the thermodynamics only through b.
 
+* Kernel diagnostic (Sec. 3.1.2, the Jackson kernel paragraph, and Sec. 4): the
+  same moments turned into thermodynamics with and without the Jackson kernel;
+  where the two differ the expansion order is not sufficient.
 * Coupling fits: least squares between (lnZ, E, C, chi)(T) of the model with
   couplings theta (one value per bond class) and target curves, minimised by
   gradient descent (Adam) with the gradient of the adjoint moment loop
@@ -66,6 +69,17 @@ def realisations(model, n_up, K: int, R: int, P: int, seed: int, a, b, T, mirror
             entry["dev"] = np.abs(mean - np.asarray(exact[k]))
         out[k] = entry
     return out
+
+
+def kernel_diagnostic(mu, mu_M, mu_M2, secs, T, n_quad: int = 0) -> Dict[str, dict]:
+    """Thermodynamics of the same moments without and with the Jackson kernel.
+
+    Returns {"none": thermo, "jackson": thermo, "diff": {obs: |none - jackson|}}
+    for lnZ, E, C and chi (arrays or device tensors, like api.thermo)."""
+    none = api.thermo(mu, mu_M, mu_M2, secs, T, kernel="none", n_quad=n_quad)
+    jack = api.thermo(mu, mu_M, mu_M2, secs, T, kernel="jackson", n_quad=n_quad)
+    diff = {k: abs(none[k] - jack[k]) for k in ("lnZ", "E", "C", "chi")}
+    return {"none": none, "jackson": jack, "diff": diff}
 
 
 def thermo_observer(model, n_up, K: int, R: int, seed: int, T, mirror=None,

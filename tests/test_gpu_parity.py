@@ -231,6 +231,23 @@ def test_thermo_matches_oracle(kernel, n_quad, mirror):
         assert np.array_equal(dev[q].cpu().numpy(), got[q])
 
 
+def test_kernel_diagnostic_matches_oracle():
+    """analysis.kernel_diagnostic: both kernels from the same moments, against the oracle."""
+    from paper_2104_13218_gb300 import analysis
+    model, n_up, mir, a, b, mu, muM, muM2 = _thermo_case("none", 0, True)
+    T = W.log_grid(0.05, 10.0, 50)
+    secs = kpm.sector_set(10, n_up, a, b, mir)
+    got = analysis.kernel_diagnostic(mu, muM, muM2, secs, T)
+    runs = [{"mu": m} for m in mu]
+    for kernel in ("none", "jackson"):
+        ref = O.thermo_from_runs(10, n_up, runs, a, b, T, kernel=kernel, mirror=mir)
+        for q in ("lnZ", "E", "C", "chi"):
+            err = np.abs(got[kernel][q] - ref[q]) / np.maximum(1.0, np.abs(ref[q]))
+            assert err.max() <= 1e-9, (kernel, q, err.max())
+    assert np.allclose(got["diff"]["C"], np.abs(got["none"]["C"] - got["jackson"]["C"]))
+    assert got["diff"]["C"].max() > 0
+
+
 def test_thermo_full_space_moments_match_oracle():
     w = W.workload("ring10_full")
     e = np.concatenate([O.eigenvalues(10, *w.model.arrays(), k) for k in range(11)])

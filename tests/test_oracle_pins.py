@@ -432,3 +432,41 @@ def test_ghost_dip_of_the_ladder_with_exact_traces():
     assert 1e-3 <= t_min <= 1e-2                        # located where the paper sees it
     high = T >= 0.05
     assert np.abs(dev[high]).max() < 1e-8 * np.abs(ex["C"][high]).max()
+
+
+def test_jackson_kernel_turns_the_ghost_dip_into_a_peak():
+    """Sec. 3.1.2 (the Jackson kernel paragraph): with exact traces the kernel
+    turns the ghost dip of C(T) into a ghost peak and, unlike the unsmoothed
+    expansion, deviates from exact diagonalisation at higher T as well; a
+    higher order (N_deg = 500) reduces that deviation."""
+    N = 14
+    model = W.ladder(N, 1.0, 1.0)
+    arr = model.arrays()
+    n_up = list(range(N // 2, N + 1))
+    mirror = [0 if k == N // 2 else 1 for k in n_up]
+    dims, mult, m1, m2 = O.sector_weights(N, n_up, mirror)
+    T = np.logspace(-3.5, 1.0, 46)
+    eigs = [O.eigenvalues(N, *arr, k) for k in n_up]
+    ex = O.thermo_exact(N, *arr, T, n_up=n_up, mirror=mirror)
+    low = (T >= 1e-3) & (T <= 1e-2)
+    high = T >= 0.05
+    dev = {}
+    for K in (100, 500):
+        mu, mu1, mu2, a, b = [], [], [], [], []
+        for i, e in enumerate(eigs):
+            ai, bi = O.rescale(e.min(), e.max(), 0.0)
+            x = O.exact_moments(e, ai, bi, K)
+            mu.append(x)
+            mu1.append(m1[i] * x)
+            mu2.append(m2[i] * x)
+            a.append(ai)
+            b.append(bi)
+        for kernel in ("none", "jackson"):
+            th = O.thermo(mu, mu1, mu2, dims, mult, np.array(a), np.array(b), T, K, kernel)
+            dev[K, kernel] = th["C"] - ex["C"]
+    assert dev[100, "none"][low].min() < -0.05 and dev[100, "jackson"][low].min() > 0.0
+    assert dev[100, "jackson"][low].max() > 0.05
+    peak = ex["C"].max()
+    assert np.abs(dev[100, "none"][high]).max() < 1e-10 * peak
+    assert np.abs(dev[100, "jackson"][high]).max() > 1e-3 * peak
+    assert np.abs(dev[500, "jackson"][high]).max() < 0.1 * np.abs(dev[100, "jackson"][high]).max()
