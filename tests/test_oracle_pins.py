@@ -400,45 +400,10 @@ def test_zeeman_field_in_exact_thermo():
     assert np.all(np.abs((w * Mk).sum(1) / Z) > 1e-3)  # the field polarises
 
 
-def test_ghost_dip_of_the_ladder_with_exact_traces():
-    """The "ghost dip" of Sec. 3.1.1: in the standard configuration (N_deg = 100,
-    eps = 0, N~ = 100, g_n = 1) the heat capacity of the AF two-leg ladder
-    deviates from exact diagonalisation at T ~ 1e-3 .. 1e-2 even with exact
-    (complete-basis) traces, so the deviation is systematic, while it agrees at
-    higher T.  Shown here for N = 14 (the paper's figure is for N = 16)."""
-    N = 14
-    model = W.ladder(N, 1.0, 1.0)
-    arr = model.arrays()
-    n_up = list(range(N // 2, N + 1))
-    mirror = [0 if k == N // 2 else 1 for k in n_up]
-    dims, mult, m1, m2 = O.sector_weights(N, n_up, mirror)
-    T = np.logspace(-3.5, 1.0, 46)
-    mu, mu1, mu2, a, b = [], [], [], [], []
-    for i, k in enumerate(n_up):
-        e = O.eigenvalues(N, *arr, k)
-        ai, bi = O.rescale(e.min(), e.max(), 0.0)
-        x = O.exact_moments(e, ai, bi, 100)
-        mu.append(x)
-        mu1.append(m1[i] * x)
-        mu2.append(m2[i] * x)
-        a.append(ai)
-        b.append(bi)
-    th = O.thermo(mu, mu1, mu2, dims, mult, np.array(a), np.array(b), T, 100, "none")
-    ex = O.thermo_exact(N, *arr, T, n_up=n_up, mirror=mirror)
-    dev = th["C"] - ex["C"]
-    low = (T >= 1e-3) & (T <= 1e-2)
-    assert dev[low].min() < -0.05                       # a dip well below the exact C ~ 0
-    t_min = T[np.argmin(dev)]
-    assert 1e-3 <= t_min <= 1e-2                        # located where the paper sees it
-    high = T >= 0.05
-    assert np.abs(dev[high]).max() < 1e-8 * np.abs(ex["C"][high]).max()
-
-
-def test_jackson_kernel_turns_the_ghost_dip_into_a_peak():
-    """Sec. 3.1.2 (the Jackson kernel paragraph): with exact traces the kernel
-    turns the ghost dip of C(T) into a ghost peak and, unlike the unsmoothed
-    expansion, deviates from exact diagonalisation at higher T as well; a
-    higher order (N_deg = 500) reduces that deviation."""
+@pytest.fixture(scope="module")
+def ladder14():
+    """Exact spectra of the AF two-leg ladder N = 14 (sectors M >= 0, M > 0 mirrored)
+    and a helper giving C(T) from exact (complete-basis) traces minus the exact C(T)."""
     N = 14
     model = W.ladder(N, 1.0, 1.0)
     arr = model.arrays()
@@ -448,25 +413,69 @@ def test_jackson_kernel_turns_the_ghost_dip_into_a_peak():
     T = np.logspace(-3.5, 1.0, 46)
     eigs = [O.eigenvalues(N, *arr, k) for k in n_up]
     ex = O.thermo_exact(N, *arr, T, n_up=n_up, mirror=mirror)
-    low = (T >= 1e-3) & (T <= 1e-2)
-    high = T >= 0.05
-    dev = {}
-    for K in (100, 500):
+
+    def deviation(K, kernel="none", eps=0.0, n_quad=None):
         mu, mu1, mu2, a, b = [], [], [], [], []
         for i, e in enumerate(eigs):
-            ai, bi = O.rescale(e.min(), e.max(), 0.0)
+            ai, bi = O.rescale(e.min(), e.max(), eps)
             x = O.exact_moments(e, ai, bi, K)
             mu.append(x)
             mu1.append(m1[i] * x)
             mu2.append(m2[i] * x)
             a.append(ai)
             b.append(bi)
-        for kernel in ("none", "jackson"):
-            th = O.thermo(mu, mu1, mu2, dims, mult, np.array(a), np.array(b), T, K, kernel)
-            dev[K, kernel] = th["C"] - ex["C"]
+        th = O.thermo(mu, mu1, mu2, dims, mult, np.array(a), np.array(b), T,
+                      K if n_quad is None else n_quad, kernel)
+        return th["C"] - ex["C"]
+
+    return {"T": T, "exact": ex, "deviation": deviation}
+
+
+def test_ghost_dip_of_the_ladder_with_exact_traces(ladder14):
+    """The "ghost dip" of Sec. 3.1.1: in the standard configuration (N_deg = 100,
+    eps = 0, N~ = 100, g_n = 1) the heat capacity of the AF two-leg ladder
+    deviates from exact diagonalisation at T ~ 1e-3 .. 1e-2 even with exact
+    (complete-basis) traces, so the deviation is systematic, while it agrees at
+    higher T.  Shown here for N = 14 (the paper's figure is for N = 16)."""
+    T, ex = ladder14["T"], ladder14["exact"]
+    dev = ladder14["deviation"](100)
+    low = (T >= 1e-3) & (T <= 1e-2)
+    assert dev[low].min() < -0.05                       # a dip well below the exact C ~ 0
+    t_min = T[np.argmin(dev)]
+    assert 1e-3 <= t_min <= 1e-2                        # located where the paper sees it
+    high = T >= 0.05
+    assert np.abs(dev[high]).max() < 1e-8 * np.abs(ex["C"][high]).max()
+
+
+def test_jackson_kernel_turns_the_ghost_dip_into_a_peak(ladder14):
+    """Sec. 3.1.2 (the Jackson kernel paragraph): with exact traces the kernel
+    turns the ghost dip of C(T) into a ghost peak and, unlike the unsmoothed
+    expansion, deviates from exact diagonalisation at higher T as well; a
+    higher order (N_deg = 500) reduces that deviation."""
+    T, ex = ladder14["T"], ladder14["exact"]
+    low = (T >= 1e-3) & (T <= 1e-2)
+    high = T >= 0.05
+    dev = {(K, k): ladder14["deviation"](K, k) for K in (100, 500) for k in ("none", "jackson")}
     assert dev[100, "none"][low].min() < -0.05 and dev[100, "jackson"][low].min() > 0.0
     assert dev[100, "jackson"][low].max() > 0.05
     peak = ex["C"].max()
     assert np.abs(dev[100, "none"][high]).max() < 1e-10 * peak
     assert np.abs(dev[100, "jackson"][high]).max() > 1e-3 * peak
     assert np.abs(dev[500, "jackson"][high]).max() < 0.1 * np.abs(dev[100, "jackson"][high]).max()
+
+
+def test_order_eps_and_quadrature_points(ladder14):
+    """Sec. 3.1.2 with exact traces: a higher order N_deg pushes the ghost dip to
+    lower T; eps > 0 makes C worse (eps = 0 is best, with eps ~ 1e-6 marginally
+    shallower); N~ below N_deg breaks the quadrature while N~ >= N_deg works."""
+    T = ladder14["T"]
+    dev = ladder14["deviation"]
+    t_min = [T[np.argmin(dev(K))] for K in (50, 100, 200, 400)]
+    assert all(t1 < t0 for t0, t1 in zip(t_min, t_min[1:]))
+    d0 = np.abs(dev(100)).max()
+    for eps in (0.01, 0.05):
+        assert np.abs(dev(100, eps=eps)).max() > 10 * d0
+    assert dev(100, eps=1e-6).min() > dev(100).min()
+    assert np.abs(dev(100, n_quad=50)).max() > 100 * d0
+    for nq in (150, 200):
+        assert np.abs(dev(100, n_quad=nq)).max() < 2 * d0
