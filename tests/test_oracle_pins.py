@@ -479,3 +479,37 @@ def test_order_eps_and_quadrature_points(ladder14):
     assert np.abs(dev(100, n_quad=50)).max() > 100 * d0
     for nq in (150, 200):
         assert np.abs(dev(100, n_quad=nq)).max() < 2 * d0
+
+
+def test_statistical_error_of_C_scales_as_inverse_sqrt_R():
+    """Statistical deviations (Sec. 3.1.1, Eq. E-3-1 .. E-3-3): over independent
+    realisations the spread of the estimated heat capacity falls like 1/sqrt(R)
+    (R = 4 -> 64 divides it by ~4), and the realisation mean stays within a few
+    standard errors of exact diagonalisation (the estimator is unbiased up to the
+    small systematic part at these T)."""
+    N = 10
+    model = W.ladder(N, 1.0, 1.0)
+    arr = model.arrays()
+    n_up = list(range(N // 2, N + 1))
+    mirror = [0 if k == N // 2 else 1 for k in n_up]
+    T = np.array([0.3, 0.6, 1.0, 2.0])
+    a, b = [], []
+    for k in n_up:
+        e = O.eigenvalues(N, *arr, k)
+        ai, bi = O.rescale(e.min(), e.max(), 0.0)
+        a.append(ai)
+        b.append(bi)
+    ex = O.thermo_exact(N, *arr, T, n_up=n_up, mirror=mirror)
+    P = 12
+    std, mean = {}, {}
+    for R in (4, 64):
+        C = []
+        for p in range(P):
+            runs = [O.sector_moments(arr, N, k, a[i], b[i], 100, R, 100 + p) for i, k in enumerate(n_up)]
+            C.append(O.thermo_from_runs(N, n_up, runs, np.array(a), np.array(b), T, mirror=mirror)["C"])
+        C = np.array(C)
+        std[R], mean[R] = C.std(axis=0), C.mean(axis=0)
+    ratio = np.exp(np.log(std[4] / std[64]).mean())
+    assert 2.5 < ratio < 6.5, ratio
+    for R in (4, 64):
+        assert np.all(np.abs(mean[R] - ex["C"]) < 4 * std[R] / np.sqrt(P) + 1e-3)
