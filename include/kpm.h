@@ -137,6 +137,13 @@ size_t kpm_bounds_workspace_size(const kpm_model *model, int32_t n_sectors, cons
  *   on_device     -- 1 if mu, mu_M, mu_M2 are device pointers.
  * Returns KPM_EBOUNDS (moments still written) when some |mu_n| > 1 + 1e-6.
  * Workspace: kpm_moments_workspace_size.
+ * Streams: with KPM_FP32, sectors of fewer than 1024 states are computed in
+ * FP64 (FP32 rounding would stay coherent there); when such sectors come
+ * with larger ones, their launches go to an internal non-blocking,
+ * lowest-priority stream of the current device (created on the first such
+ * call and kept until exit), forked from `stream` and joined back into it
+ * with events.  Like every call here, kpm_moments synchronises `stream`
+ * before it returns, so all of its work has finished by then.
  */
 int kpm_moments(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
                 const double *a, const double *b, double eps, int32_t n_moments, int32_t R,
