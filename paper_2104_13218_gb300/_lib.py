@@ -28,6 +28,8 @@ KPM_FP64 = 0
 KPM_FP32 = 1
 KPM_KERNEL_NONE = 0
 KPM_KERNEL_JACKSON = 1
+KPM_VECTORS_RADEMACHER = 0
+KPM_VECTORS_BASIS = 1
 
 STATUS_NAMES = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA",
                 5: "KPM_ENOTCONV", 6: "KPM_EBOUNDS"}
@@ -36,6 +38,16 @@ STATUS_NAMES = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA",
 class KpmModel(ctypes.Structure):
     _fields_ = [("n_sites", c_int32), ("n_bonds", c_int32), ("bi", c_void_p), ("bj", c_void_p),
                 ("J", c_void_p)]
+
+
+class KpmOpts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("vectors", c_int32), ("per_vector", c_int32),
+                ("tuned", c_int32), ("ckpt_interval", c_int32), ("reserved", c_int32 * 3)]
+
+
+class KpmSpinModel(ctypes.Structure):
+    _fields_ = [("n_sites", c_int32), ("n_bonds", c_int32), ("two_s", c_int32), ("pad", c_int32),
+                ("bi", c_void_p), ("bj", c_void_p), ("J", c_void_p)]
 
 
 P = c_void_p
@@ -60,6 +72,27 @@ PROTOTYPES = {
     "kpm_moments_static": (c_int32, [P, c_int32, P, P, P, c_int32, c_int32, c_uint64, c_uint64,
                                      c_int32, P, P, P, P]),
     "kpm_static_scratch_bytes": (c_size_t, []),
+    "kpm_moments_ex": (c_int32, [P, c_int32, P, P, P, c_double, c_int32, c_int32, c_uint64,
+                                 c_uint64, P, P, P, P, P, c_int32, P, c_size_t, P]),
+    "kpm_moments_ex_workspace_size": (c_size_t, [P, c_int32, P, c_int32, c_int32, P]),
+    "kpm_autotune": (c_int32, [P, c_int32, P, P, P, c_int32, c_int32, c_int32, P, P, P, c_size_t,
+                               P]),
+    "kpm_moments_backward_ex": (c_int32, [P, P, c_int32, c_int32, P, P, P, c_int32, c_int32,
+                                          c_uint64, c_uint64, P, P, P, P, P, c_int32, P, c_size_t,
+                                          P]),
+    "kpm_thermo_ex": (c_int32, [c_int32, c_int32, P, P, P, P, P, P, P, P, c_double, c_int32,
+                                c_int32, c_int32, P, P, P, P, P, P, c_int32, P]),
+    "kpm_thermo_backward_ex": (c_int32, [c_int32, c_int32, P, P, P, P, P, P, P, P, c_double,
+                                         c_int32, c_int32, c_int32, P, P, P, P, P, P, P, P,
+                                         c_int32, P]),
+    "kpm_realisations": (c_int32, [c_int32, c_int32, c_int32, c_int32, P, P, P, P, P, P, c_double,
+                                   c_int32, c_int32, c_int32, P, P, P, P, P, P, c_int32, P]),
+    "kpm_fp64_peak": (c_int32, [P, P, P]),
+    "kpm_spin_sector_dim": (c_int64, [c_int32, c_int32, c_int32]),
+    "kpm_spin_bounds": (c_int32, [P, c_int32, P, c_double, c_int32, c_double, c_uint64, P, P, P, P,
+                                  P]),
+    "kpm_spin_moments": (c_int32, [P, c_int32, P, P, P, c_int32, c_int32, c_uint64, c_uint64,
+                                   c_int32, P, P, P, c_int32, P]),
     "kpm_profile_enable": (c_int32, [c_int32]),
     "kpm_profile_read": (c_int32, [P, P, P]),
 }

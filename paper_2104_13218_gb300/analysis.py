@@ -1,16 +1,15 @@
-"""Studies built from the GPU moment loop: realisation statistics, a Zeeman field
-and fits of the couplings to thermodynamic curves.
+"""Studies built from the GPU moment loop: realisation statistics, a Zeeman field,
+the kernel diagnostic and fits of the couplings to thermodynamic curves.
 
 * Realisations (Sec. 3, Eq. E-3-1 to E-3-3): P independent realisations of
-  the trace estimator, each with R random vectors (realisation i uses
-  vectors i*R .. i*R + R - 1), give per temperature the mean O-bar, the
-  variance dO^2 = mean(O^2) - O-bar^2 and, against an exact curve, the
-  systematic deviation |O-bar - O_exact|.
-* Zeeman term g mu_B B sum_i s^z_i (Eq. E-3-1-1): within the sector of
-  magnetisation M it adds h M to every energy (h = g mu_B B), so the
-  moments of (H + h M - b')/a with b' = b + h M are those of (H - b)/a and
-  the field enters the thermodynamics only through b.
-
+  the trace estimator, each with R random vectors (realisation i uses vectors
+  i*R .. i*R + R - 1), come from ONE moment run with P*R vectors and
+  per-vector moments; the library then forms each realisation's
+  thermodynamics and, per temperature, the mean, the variance and (against an
+  exact curve) the systematic deviation (kpm_realisations).
+* Zeeman term g mu_B B sum_i s^z_i (Eq. E-3-1-1): it commutes with H, so the
+  moments do not change and the library's thermodynamics takes the field
+  h = g mu_B B as an argument (kpm_thermo_ex).
 * Kernel diagnostic (Sec. 3.1.2, the Jackson kernel paragraph, and Sec. 4): the
   same moments turned into thermodynamics with and without the Jackson kernel;
   where the two differ the expansion order is not sufficient.
@@ -20,8 +19,8 @@ and fits of the couplings to thermodynamic curves.
   (chebyshev_thermo).  The paper fits nothing; this uses its thermodynamics
   (Eq. E-2-2, E-2-2-B, E-2-2-C) as the model of the data.
 
-The moments and thermodynamics are computed by the library; this module only
-loops over calls and combines their outputs.
+The moments, thermodynamics and statistics are computed by the library; this
+module only sequences calls.
 """
 from __future__ import annotations
 
@@ -33,42 +32,21 @@ import torch
 from . import api
 
 
-def zeeman_shift(b: Sequence[float], n_up: Sequence[int], n_sites: int, h: float) -> np.ndarray:
-    """b + h M for every sector (M = n_up - N/2).  Full-space entries are not allowed:
-    there M varies from state to state.  Mirrored (+M/-M) entries cannot be used with
-    a field either (the two shifts differ); list both sectors instead."""
-    n_up = np.asarray(n_up)
-    if np.any(n_up < 0):
-        raise ValueError("a Zeeman shift needs S^z sectors, not the full space")
-    return np.asarray(b, dtype=np.float64) + h * (n_up - n_sites / 2.0)
-
-
 def realisations(model, n_up, K: int, R: int, P: int, seed: int, a, b, T, mirror=None,
                  kernel: str = "none", n_quad: int = 0, precision: str = "fp64",
-                 exact: Optional[Dict[str, np.ndarray]] = None) -> Dict[str, Dict[str, np.ndarray]]:
-    """Mean, variance and (with `exact`) systematic deviation over P realisations.
+                 exact: Optional[Dict[str, np.ndarray]] = None,
+                 field: float = 0.0) -> Dict[str, Dict[str, np.ndarray]]:
+    """Mean, variance and (with `exact`) systematic deviation over P realisations of R
+    vectors each, from one run with P*R vectors and per-vector moments.
 
     Returns {observable: {"mean", "var", "dev" (if exact), "all" [P, nT]}} for
-    lnZ, E, C and chi.
-    """
+    lnZ, E, C and chi (numpy arrays)."""
+    mom = api.moments(model, n_up, K, P * R, seed, a=a, b=b, precision=precision, device=True,
+                      weighted=False, per_vector=True, allow_ebounds=True)
     secs = api.sector_set(model.n_sites, n_up, a, b, mirror)
-    samples = {k: [] for k in ("lnZ", "E", "C", "chi")}
-    for i in range(P):
-        mom = api.moments(model, n_up, K, R, seed, a=a, b=b, r0=i * R, precision=precision,
-                          device=True, allow_ebounds=True)
-        th = api.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, T, kernel=kernel,
-                        n_quad=n_quad)
-        for k in samples:
-            samples[k].append(th[k].cpu().numpy())
-    out = {}
-    for k, vals in samples.items():
-        arr = np.array(vals)
-        mean = arr.mean(axis=0)
-        entry = {"mean": mean, "var": (arr ** 2).mean(axis=0) - mean ** 2, "all": arr}
-        if exact is not None and k in exact:
-            entry["dev"] = np.abs(mean - np.asarray(exact[k]))
-        out[k] = entry
-    return out
+    st = api.realisations(mom["mu_r"], secs, T, R_per=R, kernel=kernel, n_quad=n_quad,
+                          exact=exact, field=field)
+    return {k: {q: v.cpu().numpy() for q, v in d.items()} for k, d in st.items()}
 
 
 def kernel_diagnostic(mu, mu_M, mu_M2, secs, T, n_quad: int = 0) -> Dict[str, dict]:

@@ -19,7 +19,13 @@
 // resets the pair (v_{n-1}, v_n) from the copies stored every ckpt_interval
 // steps of the forward pass, which bounds the round-off of the regeneration.
 // <lambda_{n+1}, H_b v_n> = sum_s v_n(s) [H_b lambda_{n+1}](s) is accumulated
-// per parameter class from the gathers of lambda_{n+1}.
+// from the gathers of lambda_{n+1}: per parameter class in registers when
+// there are at most kMaxClasses classes, and otherwise per bond (up to 256),
+// in per-warp shared-memory slots fed by a warp-wide butterfly sum of each
+// bond's term; the tile's bond sums are then added per class.  With
+// own(s) = <v_n(s), lambda_{n+1}(s)>, the term of bond b at state s is
+// own(s)/4 if its bits agree and <v_n(s), lambda_{n+1}(s ^ mask_b)>/2 -
+// own(s)/4 if they differ.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,11 +44,12 @@ struct AdjArgs {
   TablesDev tb;
   const double *G[3];  // cotangents [sector][K] (NULL = 0)
   const double *hbar;  // [sector][3]
-  double *gpart;       // [n_tiles][kMaxClasses]
+  double *gpart;       // [n_tiles][pstride]: per class (few classes) or per bond (many)
   int *queue;
   int n, S, K, mode;   // mode 0: lambda_S = d_S; 1: general step; 2: gradient of n = 0
   int lz_zero;         // lambda_{n+2} = 0
   int Rp, G_lanes, gpw, n_classes;
+  int pstride;         // entries per tile in gpart
   int cstart[kMaxClasses + 1];
   double half_n;
 };
@@ -181,11 +188,145 @@ __global__ void __launch_bounds__(kThreads)
       block_sum<kMaxClasses>(acc, s_red);
       if (threadIdx.x == 0) {
         const double f = (a.mode == 2 ? 1.0 : 2.0) * sd.inv_a;
-        for (int p = 0; p < a.n_classes; ++p) a.gpart[(int64_t)t * kMaxClasses + p] += f * acc[p];
+        for (int p = 0; p < a.n_classes; ++p) a.gpart[(int64_t)t * a.pstride + p] += f * acc[p];
       }
     } else {
       __syncthreads();
     }
+  }
+}
+
+// The same step with per-bond sums (more than kMaxClasses parameter classes).
+// The loop over a warp's states is warp-uniform so that every lane takes
+// part in the per-bond butterfly sums.
+template <int CPL>
+__global__ void __launch_bounds__(kThreads)
+    adjoint_step_bonds_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ BondsDev bd) {
+  using V = double2;
+  extern __shared__ double s_acc[];  // [kWarps][n_bonds]
+  __shared__ int s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = a.G_lanes;
+  const int grp = lane / G, sub = lane - grp * G;
+  const bool active = grp < a.gpw;
+  const int64_t crow = a.Rp / 2;
+  const int nb = bd.n_bonds;
+  double *wacc = s_acc + warp * nb;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
+    for (int b = lane; b < nb; b += 32) wacc[b] = 0.0;
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.tb.n_tiles) break;
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const int sec = tile.sector;
+    const int n = a.n;
+    double w4[3], w2p[3], wc[3];
+    for (int q = 0; q < 3; ++q) {
+      w4[q] = 4.0 * cot_at(a.G[q], sec, a.K, 2 * n);
+      w2p[q] = 2.0 * cot_at(a.G[q], sec, a.K, 2 * n + 1);
+      wc[q] = (n >= 2) ? 2.0 * cot_at(a.G[q], sec, a.K, 2 * n - 1) : a.hbar[sec * 3 + q];
+    }
+    const double A = 2.0 * sd.inv_a;
+    const bool full_tile = sd.n_up < 0;
+    uint32_t hb = tile.b_first;
+    for (uint32_t ub = warp * a.gpw; ub < tile.count; ub += kWarps * a.gpw) {
+      const uint32_t u = ub + grp;
+      const bool valid = active && u < tile.count;
+      const int64_t row = tile.row0 + u;
+      uint64_t s = 0;
+      if (valid)
+        s = full_tile ? (uint64_t)(row - sd.row0)
+                      : sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+      const double M = full_tile ? (double)__popcll(s) - a.half_n : sd.Mval;
+      const double c4 = w4[0] + M * (w4[1] + M * w4[2]);
+      const double c2p = w2p[0] + M * (w2p[1] + M * w2p[2]);
+      const double cm = wc[0] + M * (wc[1] + M * wc[2]);
+      if (a.mode == 0) {
+        if (valid) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const V v = a.Vg[row * crow + sub + c * G];
+            a.Lo[row * crow + sub + c * G] = make_double2(cm * v.x, cm * v.y);
+          }
+        }
+        continue;
+      }
+      V vn[CPL], lo[CPL], hv[CPL], hl[CPL];
+      double own = 0.0;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        vn[c] = make_double2(0.0, 0.0);
+        lo[c] = make_double2(0.0, 0.0);
+        hv[c] = make_double2(0.0, 0.0);
+        hl[c] = make_double2(0.0, 0.0);
+        if (valid) {
+          vn[c] = a.Vg[row * crow + sub + c * G];
+          lo[c] = a.Lg[row * crow + sub + c * G];
+          own = fma(vn[c].x, lo[c].x, fma(vn[c].y, lo[c].y, own));
+        }
+      }
+      double d = bd.J_quarter_sum;
+      for (int b = 0; b < nb; ++b) {
+        double term = 0.0;
+        if (valid) {
+          const uint64_t m = bd.mask[b];
+          const uint64_t tt = s & m;
+          if (tt != 0 && tt != m) {
+            d -= 0.5 * bd.J[b];
+            const uint64_t f = s ^ m;
+            const int64_t nr = sd.row0 + (full_tile ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+            const double jh = 0.5 * bd.J[b];
+            double tnb = 0.0;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              const V l = __ldg(a.Lg + nr * crow + sub + c * G);
+              hl[c].x = fma(jh, l.x, hl[c].x);
+              hl[c].y = fma(jh, l.y, hl[c].y);
+              tnb = fma(vn[c].x, l.x, fma(vn[c].y, l.y, tnb));
+              if (a.mode == 1) {
+                const V v = __ldg(a.Vg + nr * crow + sub + c * G);
+                hv[c].x = fma(jh, v.x, hv[c].x);
+                hv[c].y = fma(jh, v.y, hv[c].y);
+              }
+            }
+            term = 0.5 * tnb - 0.25 * own;
+          } else {
+            term = 0.25 * own;
+          }
+        }
+        term = warp_sum(term);  // lane 0 holds the warp's sum for bond b
+        if (lane == 0) wacc[b] += term;
+      }
+      if (valid && a.mode == 1) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int64_t idx = row * crow + sub + c * G;
+          const V vp = a.Vo[idx];
+          V vm;
+          vm.x = A * (fma(d, vn[c].x, hv[c].x) - sd.b * vn[c].x) - vp.x;
+          vm.y = A * (fma(d, vn[c].y, hv[c].y) - sd.b * vn[c].y) - vp.y;
+          a.Vo[idx] = vm;
+          V lz = make_double2(0.0, 0.0);
+          if (!a.lz_zero) lz = a.Lo[idx];
+          V ln;
+          ln.x = c4 * vn[c].x + c2p * vp.x + cm * vm.x + A * (fma(d, lo[c].x, hl[c].x) - sd.b * lo[c].x) - lz.x;
+          ln.y = c4 * vn[c].y + c2p * vp.y + cm * vm.y + A * (fma(d, lo[c].y, hl[c].y) - sd.b * lo[c].y) - lz.y;
+          a.Lo[idx] = ln;
+        }
+      }
+    }
+    __syncthreads();
+    if (a.mode != 0) {
+      const double f = (a.mode == 2 ? 1.0 : 2.0) * sd.inv_a;
+      for (int b = threadIdx.x; b < nb; b += kThreads) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += s_acc[w * nb + b];
+        a.gpart[(int64_t)t * a.pstride + b] += f * v;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -204,14 +345,16 @@ __global__ void adjoint_hbar_kernel(const double *g0, const double *g1, const do
   hbar[i] = h;
 }
 
-// dL/dtheta_p = (1/R) sum over tiles (tile order) of gpart[t][p]; the 1/R is the
-// average over the random vectors in mu_n = (1/R) sum_r <r|T_n|r>, left out of
-// the per-vector recursion above.
-__global__ void adjoint_final_kernel(const double *gpart, int n_tiles, int P, double inv_R,
-                                     double *out) {
+// dL/dtheta_p = (1/R) sum over tiles (tile order) of the entries e in
+// [estart[p], estart[p+1]) of gpart[t][e] (the class itself, or the class's
+// bonds); the 1/R is the average over the random vectors in
+// mu_n = (1/R) sum_r <r|T_n|r>, left out of the per-vector recursion above.
+__global__ void adjoint_final_kernel(const double *gpart, int n_tiles, int pstride,
+                                     const int *estart, double inv_R, double *out) {
   const int p = blockIdx.x;
   double v = 0.0;
-  for (int t = threadIdx.x; t < n_tiles; t += 32) v += gpart[(int64_t)t * kMaxClasses + p];
+  for (int e = estart[p]; e < estart[p + 1]; ++e)
+    for (int t = threadIdx.x; t < n_tiles; t += 32) v += gpart[(int64_t)t * pstride + e];
   v = warp_sum(v);
   if (threadIdx.x == 0) out[p] = v * inv_R;
 }
@@ -221,6 +364,21 @@ namespace {
 template <int CPL, bool FULL>
 void *adj_ptr() {
   return reinterpret_cast<void *>(&adjoint_step_kernel<CPL, FULL>);
+}
+
+template <int CPL>
+void *adjb_ptr() {
+  return reinterpret_cast<void *>(&adjoint_step_bonds_kernel<CPL>);
+}
+
+void *pick_adj_bonds(int cpl) {
+  switch (cpl) {
+    case 1: return adjb_ptr<1>();
+    case 2: return adjb_ptr<2>();
+    case 3: return adjb_ptr<3>();
+    case 4: return adjb_ptr<4>();
+    default: return adjb_ptr<8>();
+  }
 }
 
 void *pick_adj(int cpl, bool full) {
@@ -239,18 +397,21 @@ struct AdjPlan {
   std::vector<int32_t> bi, bj;
   std::vector<double> J;
   int cstart[kMaxClasses + 1];
+  std::vector<int> estart;       // per class: first entry of gpart (class or bond index)
   int n_classes = 0;
+  bool by_bond = false;          // more than kMaxClasses classes: per-bond sums
+  int pstride = kMaxClasses;
   int k = 32, n_ckpt = 0;
   size_t bytes = 0;
 };
 
 int prepare_adjoint(const kpm_model *m, const int32_t *bond_class, int n_classes, int n_sectors,
-                    const int32_t *n_up, int K, int R, int ckpt, AdjPlan *ap) {
+                    const int32_t *n_up, int K, int R, int ckpt, AdjPlan *ap,
+                    int vectors = kVecRademacher) {
   KPM_TRY(validate_model(m));
   int P = n_classes;
   if (bond_class == nullptr) P = m->n_bonds;
-  KPM_REQUIRE(P >= 1 && P <= kMaxClasses, KPM_EINVAL, "n_classes = %d outside 1..%d", P,
-              kMaxClasses);
+  KPM_REQUIRE(P >= 1 && P <= kMaxBonds, KPM_EINVAL, "n_classes = %d outside 1..%d", P, kMaxBonds);
   std::vector<int> cls(m->n_bonds);
   for (int b = 0; b < m->n_bonds; ++b) {
     cls[b] = bond_class ? bond_class[b] : b;
@@ -261,7 +422,7 @@ int prepare_adjoint(const kpm_model *m, const int32_t *bond_class, int n_classes
   ap->bj.clear();
   ap->J.clear();
   for (int p = 0; p < P; ++p) {
-    ap->cstart[p] = (int)ap->bi.size();
+    if (p < kMaxClasses) ap->cstart[p] = (int)ap->bi.size();
     for (int b = 0; b < m->n_bonds; ++b)
       if (cls[b] == p) {
         ap->bi.push_back(m->bi[b]);
@@ -269,21 +430,42 @@ int prepare_adjoint(const kpm_model *m, const int32_t *bond_class, int n_classes
         ap->J.push_back(m->J[b]);
       }
   }
+  std::vector<int> cs(P + 1);
+  {
+    // class boundaries in the class-sorted bond list, for any number of classes
+    int pos = 0;
+    for (int p = 0; p < P; ++p) {
+      cs[p] = pos;
+      for (int b = 0; b < m->n_bonds; ++b) pos += cls[b] == p ? 1 : 0;
+    }
+    cs[P] = pos;
+  }
   for (int p = P; p <= kMaxClasses; ++p) ap->cstart[p] = (int)ap->bi.size();
+  ap->by_bond = P > kMaxClasses;
+  if (ap->by_bond) {
+    ap->estart = cs;  // gpart holds per-bond sums in class-sorted bond order
+    ap->pstride = std::max(1, m->n_bonds);
+  } else {
+    ap->estart.resize(P + 1);
+    for (int p = 0; p <= P; ++p) ap->estart[p] = p;
+    ap->pstride = kMaxClasses;
+  }
   ap->sorted.n_sites = m->n_sites;
   ap->sorted.n_bonds = m->n_bonds;
   ap->sorted.bi = ap->bi.data();
   ap->sorted.bj = ap->bj.data();
   ap->sorted.J = ap->J.data();
-  KPM_TRY(prepare_run(&ap->sorted, n_sectors, n_up, K, R, KPM_FP64, &ap->run));
+  KPM_TRY(prepare_run(&ap->sorted, n_sectors, n_up, K, R, KPM_FP64, &ap->run, Knobs(), vectors));
   ap->k = ckpt > 0 ? ckpt : 32;
   ap->n_ckpt = (ap->run.S + ap->k - 1) / ap->k;
   const MomentsRun &r = ap->run;
   const size_t SK = (size_t)n_sectors * K;
   ap->bytes = run_bytes(r) + 2 * r.vec_bytes + (size_t)ap->n_ckpt * 2 * r.vec_bytes +
-              align256(std::max<size_t>(1, r.plan.tiles.size()) * kMaxClasses * 8) +
+              align256(std::max<size_t>(1, r.plan.tiles.size()) *
+                       std::max(kMaxClasses, m->n_bonds) * 8) +
               align256((size_t)n_sectors * 3 * 8) + align256((size_t)(r.S + 2) * 4) +
-              3 * align256(SK * 8) + align256(kMaxClasses * 8) + 1024;
+              3 * align256(SK * 8) + align256((size_t)kMaxBonds * 8) +
+              align256((size_t)(kMaxBonds + 1) * 4) + 1024;
   return KPM_OK;
 }
 
@@ -305,21 +487,20 @@ extern "C" size_t kpm_moments_backward_workspace_size(const kpm_model *model, in
   return ap.bytes;
 }
 
-extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_class,
-                                    int32_t n_classes, int32_t n_sectors, const int32_t *n_up,
-                                    const double *a, const double *b, int32_t n_moments, int32_t R,
-                                    uint64_t seed, uint64_t r0, int32_t precision,
-                                    int32_t ckpt_interval, const double *dL_dmu,
-                                    const double *dL_dmu_M, const double *dL_dmu_M2,
-                                    double *dL_dtheta, int32_t on_device, void *workspace,
-                                    size_t ws_bytes, void *stream_ptr) {
-  clear_error();
+namespace {
+
+int backward_impl(const kpm_model *model, const int32_t *bond_class, int32_t n_classes,
+                  int32_t n_sectors, const int32_t *n_up, const double *a, const double *b,
+                  int32_t n_moments, int32_t R, uint64_t seed, uint64_t r0, int32_t precision,
+                  int32_t vectors, int32_t ckpt_interval, const double *dL_dmu,
+                  const double *dL_dmu_M, const double *dL_dmu_M2, double *dL_dtheta,
+                  int32_t on_device, void *workspace, size_t ws_bytes, void *stream_ptr) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
   KPM_REQUIRE(precision == KPM_FP64, KPM_EINVAL, "the adjoint runs in FP64 only");
   KPM_REQUIRE(a && b && dL_dmu && dL_dtheta, KPM_EINVAL, "NULL argument");
   AdjPlan ap;
   KPM_TRY(prepare_adjoint(model, bond_class, n_classes, n_sectors, n_up, n_moments, R,
-                          ckpt_interval, &ap));
+                          ckpt_interval, &ap, vectors));
   MomentsRun &run = ap.run;
   Workspace ws;
   KPM_TRY(ws.acquire(workspace, ws_bytes, ap.bytes, stream));
@@ -329,13 +510,15 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
   double2 *LB = arena.take<double2>(run.vec_bytes / 16);
   std::vector<char *> ck(2 * ap.n_ckpt);
   for (auto &p : ck) p = arena.take<char>(run.vec_bytes);
-  double *gpart = arena.take<double>(std::max<size_t>(1, run.plan.tiles.size()) * kMaxClasses);
+  const size_t n_gpart = std::max<size_t>(1, run.plan.tiles.size()) * ap.pstride;
+  double *gpart = arena.take<double>(n_gpart);
+  int *estart = arena.take<int>(ap.estart.size());
   double *hbar = arena.take<double>((size_t)n_sectors * 3);
   int *queues = arena.take<int>((size_t)run.S + 2);
   const size_t SK = (size_t)n_sectors * n_moments;
   double *dg[3] = {nullptr, nullptr, nullptr};
-  double *dtheta = arena.take<double>(kMaxClasses);
-  bool ok = LA && LB && gpart && hbar && queues && dtheta;
+  double *dtheta = arena.take<double>(std::max(kMaxClasses, ap.n_classes));
+  bool ok = LA && LB && gpart && estart && hbar && queues && dtheta;
   for (auto p : ck) ok = ok && p;
   const double *gin[3] = {dL_dmu, dL_dmu_M, dL_dmu_M2};
   for (int q = 0; q < 3; ++q) {
@@ -349,7 +532,9 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
     }
   }
   KPM_REQUIRE(ok, KPM_ENOMEM, "workspace too small for the adjoint");
-  KPM_CUDA(cudaMemsetAsync(gpart, 0, std::max<size_t>(1, run.plan.tiles.size()) * kMaxClasses * 8, stream));
+  KPM_CUDA(cudaMemsetAsync(gpart, 0, n_gpart * 8, stream));
+  KPM_CUDA(cudaMemcpyAsync(estart, ap.estart.data(), ap.estart.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, stream));
   KPM_CUDA(cudaMemsetAsync(queues, 0, ((size_t)run.S + 2) * 4, stream));
   adjoint_hbar_kernel<<<(n_sectors * 3 + 127) / 128, 128, 0, stream>>>(dg[0], dg[1], dg[2], hbar,
                                                                        n_sectors, n_moments);
@@ -385,11 +570,13 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
   ar.G_lanes = run.lay.G;
   ar.gpw = run.lay.gpw;
   ar.n_classes = ap.n_classes;
+  ar.pstride = ap.pstride;
   for (int p = 0; p <= kMaxClasses; ++p) ar.cstart[p] = ap.cstart[p];
   ar.half_n = 0.5 * run.plan.N;
-  void *fn = pick_adj(run.lay.cpl, run.plan.any_full);
+  void *fn = ap.by_bond ? pick_adj_bonds(run.lay.cpl) : pick_adj(run.lay.cpl, run.plan.any_full);
+  const size_t smem = ap.by_bond ? (size_t)kWarps * std::max(1, model->n_bonds) * sizeof(double) : 0;
   int per_sm = 0;
-  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+  KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -406,7 +593,7 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
     ar.lz_zero = lz_zero;
     ar.queue = queues + qslot;
     void *args[] = {(void *)&ar, (void *)&run.bonds};
-    KPM_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream));
+    KPM_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, stream));
     count_launches(1);
     return KPM_OK;
   };
@@ -431,7 +618,7 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
   // n = 0: (1/a) <lambda_1, H_b v_0> with Vg = v_0, Lg = lambda_1
   KPM_TRY(launch(2, 0, Vg, Vo, Lg, Lo, 1, 0));
   adjoint_final_kernel<<<ap.n_classes, 32, 0, stream>>>(gpart, (int)run.plan.tiles.size(),
-                                                        ap.n_classes, 1.0 / R, dtheta);
+                                                        ap.pstride, estart, 1.0 / R, dtheta);
   KPM_CUDA(cudaGetLastError());
   count_launches(1);
   if (on_device)
@@ -440,4 +627,39 @@ extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_
     KPM_CUDA(cudaMemcpyAsync(dL_dtheta, dtheta, ap.n_classes * 8, cudaMemcpyDeviceToHost, stream));
   KPM_CUDA(cudaStreamSynchronize(stream));
   return KPM_OK;
+}
+
+}  // namespace
+
+extern "C" int kpm_moments_backward(const kpm_model *model, const int32_t *bond_class,
+                                    int32_t n_classes, int32_t n_sectors, const int32_t *n_up,
+                                    const double *a, const double *b, int32_t n_moments, int32_t R,
+                                    uint64_t seed, uint64_t r0, int32_t precision,
+                                    int32_t ckpt_interval, const double *dL_dmu,
+                                    const double *dL_dmu_M, const double *dL_dmu_M2,
+                                    double *dL_dtheta, int32_t on_device, void *workspace,
+                                    size_t ws_bytes, void *stream_ptr) {
+  clear_error();
+  return backward_impl(model, bond_class, n_classes, n_sectors, n_up, a, b, n_moments, R, seed, r0,
+                       precision, KPM_VECTORS_RADEMACHER, ckpt_interval, dL_dmu, dL_dmu_M,
+                       dL_dmu_M2, dL_dtheta, on_device, workspace, ws_bytes, stream_ptr);
+}
+
+extern "C" int kpm_moments_backward_ex(const kpm_model *model, const int32_t *bond_class,
+                                       int32_t n_classes, int32_t n_sectors, const int32_t *n_up,
+                                       const double *a, const double *b, int32_t n_moments,
+                                       int32_t R, uint64_t seed, uint64_t r0,
+                                       const kpm_opts *opts, const double *dL_dmu,
+                                       const double *dL_dmu_M, const double *dL_dmu_M2,
+                                       double *dL_dtheta, int32_t on_device, void *workspace,
+                                       size_t ws_bytes, void *stream_ptr) {
+  clear_error();
+  kpm_opts o{};
+  if (opts) o = *opts;
+  KPM_REQUIRE(o.vectors == KPM_VECTORS_RADEMACHER || o.vectors == KPM_VECTORS_BASIS, KPM_EINVAL,
+              "vectors %d", o.vectors);
+  KPM_REQUIRE(o.per_vector == 0, KPM_EINVAL, "the adjoint has no per-vector form");
+  return backward_impl(model, bond_class, n_classes, n_sectors, n_up, a, b, n_moments, R, seed, r0,
+                       o.precision, o.vectors, o.ckpt_interval, dL_dmu, dL_dmu_M, dL_dmu_M2,
+                       dL_dtheta, on_device, workspace, ws_bytes, stream_ptr);
 }

@@ -125,8 +125,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-namespace {
-
 // Number of eigenvalues of the m x m tridiagonal (alpha, beta) below x.
 int sturm_count(const std::vector<double> &al, const std::vector<double> &be, int m, double x) {
   int count = 0;
@@ -184,6 +182,8 @@ double ritz_last_component(const std::vector<double> &al, const std::vector<doub
   }
   return std::fabs(y[m - 1]);
 }
+
+namespace {
 
 int sm_count_b() {
   int dev = 0, n = 0;

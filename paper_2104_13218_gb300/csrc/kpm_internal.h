@@ -205,6 +205,13 @@ struct RowLayout {
 };
 int make_layout(int R, int precision, RowLayout *out);
 
+// Tridiagonal eigenvalue tools of the Lanczos bounds (diagonal al[0..m),
+// couplings be[1..m), be[i] between i-1 and i): the k-th smallest eigenvalue
+// by Sturm bisection, and |last component| of the unit eigenvector of theta.
+double tridiag_eig(const std::vector<double> &al, const std::vector<double> &be, int m, int k);
+double ritz_last_component(const std::vector<double> &al, const std::vector<double> &be, int m,
+                           double theta);
+
 // Instrumentation: count kernel launches; bracket step launches with events.
 void count_launches(int n);
 bool profiling();

@@ -787,6 +787,94 @@ __global__ void __launch_bounds__(kThreads) reduce_tile_sums_kernel(const double
   reduce_sector_tiles<NQ>(ts, tb, blockIdx.x, sums, s_red);
 }
 
+// ---------------------------------------------------------------- per-vector moments
+// The moments of each random vector separately, mu^(r)_n = <r|T_n(H')|r>
+// (the terms of the average in Eq. E-2-7), for realisation statistics and
+// sampled checks.  After a step the column kernel reads v_n and v_{n+1} once
+// more and forms, per chunk of rows of one sector, <v_n^r|v_n^r> and
+// <v_{n+1}^r|v_n^r> for every vector r in FP64; the chunk sums are then added
+// per sector in chunk order.  This costs one extra read of both vectors per
+// step and is only done when per-vector moments are asked for.
+struct ColArgs {
+  const void *x, *y;
+  const int64_t *chunks;  // (row_begin, row_end, sector) per chunk
+  double *part;           // [n_chunks][R][2]
+  int R, Rp;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) column_dots_kernel(const __grid_constant__ ColArgs a) {
+  __shared__ double s_xx[kThreads], s_yx[kThreads];
+  const int64_t ch = blockIdx.x;
+  const int64_t r_begin = a.chunks[3 * ch], r_end = a.chunks[3 * ch + 1];
+  const T *x = reinterpret_cast<const T *>(a.x);
+  const T *y = reinterpret_cast<const T *>(a.y);
+  const int cols = min(a.R, kThreads);
+  const int nl = kThreads / cols;
+  const int cl = threadIdx.x % cols, rl = threadIdx.x / cols;
+  for (int c0 = 0; c0 < a.R; c0 += cols) {
+    const int col = c0 + cl;
+    double xx = 0.0, yx = 0.0;
+    if (rl < nl && col < a.R) {
+      for (int64_t row = r_begin + rl; row < r_end; row += nl) {
+        const double xv = (double)x[row * a.Rp + col];
+        const double yv = (double)y[row * a.Rp + col];
+        xx = fma(xv, xv, xx);
+        yx = fma(yv, xv, yx);
+      }
+    }
+    s_xx[threadIdx.x] = xx;
+    s_yx[threadIdx.x] = yx;
+    __syncthreads();
+    if ((int)threadIdx.x < cols && c0 + (int)threadIdx.x < a.R) {
+      double sx = 0.0, sy = 0.0;
+      for (int l = 0; l < nl; ++l) {
+        sx += s_xx[l * cols + threadIdx.x];
+        sy += s_yx[l * cols + threadIdx.x];
+      }
+      double *o = a.part + (ch * a.R + c0 + threadIdx.x) * 2;
+      o[0] = sx;
+      o[1] = sy;
+    }
+    __syncthreads();
+  }
+}
+
+// out[sec][r][q] = sum over the sector's chunks (in order) of part[chunk][r][q].
+__global__ void __launch_bounds__(kThreads)
+    column_reduce_kernel(const double *part, const int64_t *sec_ranges, double *out, int R) {
+  const int sec = blockIdx.x;
+  const int64_t c0 = sec_ranges[2 * sec], c1 = sec_ranges[2 * sec + 1];
+  for (int i = threadIdx.x; i < 2 * R; i += kThreads) {
+    double v = 0.0;
+    for (int64_t c = c0; c < c1; ++c) v += part[c * 2 * R + i];
+    out[(int64_t)sec * 2 * R + i] = v;
+  }
+}
+
+// mu_r[out_index][r][n] from the per-vector sums (no average over r).
+struct AssembleRArgs {
+  const double *sums_r;  // [S][n_sectors][R][2]
+  const SectorDev *sectors;
+  double *mu_r;
+  int n_sectors, K, R;
+};
+
+__global__ void assemble_r_kernel(const __grid_constant__ AssembleRArgs a) {
+  const int64_t total = (int64_t)a.n_sectors * a.R * a.K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i % a.K);
+    const int r = (int)((i / a.K) % a.R);
+    const int sec = (int)(i / ((int64_t)a.K * a.R));
+    const int step = n / 2, q = n & 1;
+    const double raw = a.sums_r[(((int64_t)step * a.n_sectors + sec) * a.R + r) * 2 + q];
+    const double base = a.sums_r[((int64_t)sec * a.R + r) * 2 + q];  // mu_0 or mu_1 of vector r
+    const double val = step == 0 ? raw : 2.0 * raw - base;
+    a.mu_r[((int64_t)a.sectors[sec].out_index * a.R + r) * a.K + n] = val;
+  }
+}
+
 // ---------------------------------------------------------------- random vectors
 
 struct InitArgs {
@@ -795,6 +883,7 @@ struct InitArgs {
   uint64_t seed, r0;
   int R, Rp, G, gpw;
   int uniform;  // 0: +-1/sqrt(D) signs; 1: uniform values in (-1, 1), not normalised
+  int basis;    // 1: vector r is the unit vector of the state of rank r0 + r (zero if none)
 };
 
 template <typename T>
@@ -829,7 +918,9 @@ __global__ void __launch_bounds__(kThreads) init_vectors_kernel(const __grid_con
         for (int e = 0; e < W; ++e) {
           const int col = ch * W + e;
           T x = 0;
-          if (col < a.R) {
+          if (col < a.R && a.basis) {
+            x = (uint64_t)(row - sd.row0) == a.r0 + (uint64_t)col ? (T)1 : (T)0;
+          } else if (col < a.R) {
             const uint64_t h = splitmix64(s_hr[col] ^ s);
             if (a.uniform)
               x = (T)(2.0 * (((double)(h >> 11) + 0.5) * 0x1.0p-53) - 1.0);
@@ -950,6 +1041,8 @@ size_t step_smem(const MomentsRun &r) {
   return (size_t)r.bonds.table_size * 8;
 }
 
+}  // namespace
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -961,11 +1054,15 @@ int sm_count() {
   return n;
 }
 
-}  // namespace
-
 int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
-                int precision, MomentsRun *run) {
+                int precision, MomentsRun *run, const Knobs &knobs, int vectors,
+                bool per_vector) {
   KPM_TRY(validate_model(m));
+  KPM_REQUIRE(vectors == kVecRademacher || vectors == kVecBasis, KPM_EINVAL,
+              "vectors = %d (KPM_VECTORS_RADEMACHER or KPM_VECTORS_BASIS)", vectors);
+  run->knobs = knobs;
+  run->vectors = vectors;
+  run->per_vector = per_vector;
   KPM_TRY(validate_sectors(m, n_sectors, n_up));
   KPM_REQUIRE(K >= 2 && (K % 2) == 0, KPM_EINVAL, "n_moments = %d must be even and >= 2", K);
   KPM_TRY(make_layout(R, precision, &run->lay));
@@ -982,13 +1079,13 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   fill_pass_masks(&run->bonds, run->lay.G);
   // neighbour lists for cooperative layouts with grouped couplings (CPL 1 or 2)
   run->list_stride = 0;
-  if (run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) && run->bonds.n_groups > 0 &&
-      m->n_bonds <= 255) {
+  if (knobs.lists != 0 && run->lay.G >= 2 && (run->lay.cpl == 1 || run->lay.cpl == 2) &&
+      run->bonds.n_groups > 0 && m->n_bonds <= 255) {
     // FP32 rows of 17..32 chunks: two states per warp, 16 lanes x 2 chunks
     // each (the row layout in memory is unchanged; lanes whose second slot
     // lies past the row's chunks skip it), which halves the per-state work
     // of the warp.
-    if (precision == KPM_FP32 && run->lay.cpl == 1 && run->lay.G > 16) {
+    if (precision == KPM_FP32 && run->lay.cpl == 1 && run->lay.G > 16 && knobs.two_state != 0) {
       run->lay.G = 16;
       run->lay.cpl = 2;
       run->lay.gpw = 2;
@@ -1002,9 +1099,35 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
     }
     if (list_smem_bytes(run->lay.gpw, stride) <= kMaxListSmem) run->list_stride = stride;
   }
-  const int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
-                                          : choose_tile_states(run->lay.gpw, rows);
+  int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
+                                    : choose_tile_states(run->lay.gpw, rows);
+  if (knobs.tile_states > 0) {
+    // a tuned tile size, in whole warp groups, within the list kernel's tile limit
+    const int64_t g = run->lay.gpw;
+    ts = std::max<int64_t>(knobs.tile_states, g);
+    ts = (ts + g - 1) / g * g;
+    if (run->list_stride > 0)
+      ts = std::max<int64_t>(ts, (rows + KPM_LIST_MAX_TILES - 1) / KPM_LIST_MAX_TILES);
+  }
   KPM_TRY(build_plan(m, n_sectors, n_up, ts, &run->plan));
+  if (per_vector) {
+    // chunks of rows, each inside one sector, for the per-vector column sums
+    const int64_t ch = std::min<int64_t>(65536, std::max<int64_t>(256, run->plan.total_rows / 2048));
+    run->cd_chunks.clear();
+    std::vector<int64_t> ranges;
+    for (int sidx = 0; sidx < run->plan.n_sectors; ++sidx) {
+      const int64_t r0s = run->plan.row0[sidx], r1s = r0s + run->plan.dim[sidx];
+      ranges.push_back((int64_t)run->cd_chunks.size() / 3);
+      for (int64_t r = r0s; r < r1s; r += ch) {
+        run->cd_chunks.push_back(r);
+        run->cd_chunks.push_back(std::min(r + ch, r1s));
+        run->cd_chunks.push_back(sidx);
+      }
+      ranges.push_back((int64_t)run->cd_chunks.size() / 3);
+    }
+    run->n_cd = (int)(run->cd_chunks.size() / 3);
+    run->cd_chunks.insert(run->cd_chunks.end(), ranges.begin(), ranges.end());
+  }
   run->NQ = run->plan.any_full ? 6 : 2;
   KPM_REQUIRE((uint64_t)(run->plan.total_rows + 1) * (run->lay.Rp / run->lay.vec_width) < (1ull << 32),
               KPM_EINVAL, "%lld rows x %d chunks exceed 32-bit chunk indices",
@@ -1030,7 +1153,11 @@ size_t run_bytes(const MomentsRun &r) {
          align256((size_t)r.plan.total_rows * r.list_stride * sizeof(uint32_t)) +
          align256((lists ? 2 : 1) * r.plan.tiles.size() * r.NQ * sizeof(double)) +
          align256((size_t)r.S * r.plan.n_sectors * r.NQ * sizeof(double)) +
-         align256((size_t)2 * r.S * sizeof(int)) + 256;
+         align256((size_t)2 * r.S * sizeof(int)) + 256 +
+         (r.per_vector ? align256(r.cd_chunks.size() * sizeof(int64_t)) +
+                             align256((size_t)r.n_cd * r.lay.R * 2 * sizeof(double)) +
+                             align256((size_t)r.S * r.plan.n_sectors * r.lay.R * 2 * sizeof(double))
+                       : 0);
 }
 
 namespace {
@@ -1138,12 +1265,23 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     count_launches(1);
     KPM_TRY(upload_coefficients(r, sec, arena, s));
   }
+  if (r.per_vector) {
+    int64_t *cd = arena.take<int64_t>(r.cd_chunks.size());
+    r.cd_part = arena.take<double>((size_t)r.n_cd * r.lay.R * 2);
+    r.sums_r = arena.take<double>((size_t)r.S * r.plan.n_sectors * r.lay.R * 2);
+    KPM_REQUIRE(cd && r.cd_part && r.sums_r, KPM_ENOMEM,
+                "workspace too small for the per-vector moments");
+    KPM_CUDA(cudaMemcpyAsync(cd, r.cd_chunks.data(), r.cd_chunks.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+    r.cd_dev = cd;
+  }
   KPM_CUDA(cudaMemsetAsync(r.counters, 0, sizeof(int) * 2 * r.S, s));
   KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
   void *fn = pick_kernel(r);
   int per_sm = 0;
   KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, step_smem(r)));
   per_sm = std::max(per_sm, 1);
+  if (r.knobs.blocks_per_sm > 0) per_sm = std::min(per_sm, r.knobs.blocks_per_sm);
   r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), (int64_t)r.plan.tiles.size());
   r.grid = std::max(r.grid, 1);
   return KPM_OK;
@@ -1153,6 +1291,7 @@ int launch_init(const MomentsRun &r, void *v0, uint64_t seed, uint64_t r0, cudaS
                 bool uniform) {
   InitArgs a;
   a.uniform = uniform ? 1 : 0;
+  a.basis = (!uniform && r.vectors == kVecBasis) ? 1 : 0;
   a.v0 = v0;
   a.tb = r.tb;
   a.seed = seed;
@@ -1233,8 +1372,45 @@ int launch_finish(const MomentsRun &r, cudaStream_t s) {
   return KPM_OK;
 }
 
-int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2, cudaStream_t s) {
+int launch_column_dots(const MomentsRun &r, const void *x, const void *y, int step,
+                       cudaStream_t s) {
+  if (!r.per_vector) return KPM_OK;
+  ColArgs a;
+  a.x = x;
+  a.y = y;
+  a.chunks = r.cd_dev;
+  a.part = r.cd_part;
+  a.R = r.lay.R;
+  a.Rp = r.lay.Rp;
+  if (r.precision == KPM_FP32)
+    column_dots_kernel<float><<<r.n_cd, kThreads, 0, s>>>(a);
+  else
+    column_dots_kernel<double><<<r.n_cd, kThreads, 0, s>>>(a);
+  KPM_CUDA(cudaGetLastError());
+  double *out = r.sums_r + (size_t)step * r.plan.n_sectors * r.lay.R * 2;
+  column_reduce_kernel<<<r.plan.n_sectors, kThreads, 0, s>>>(r.cd_part, r.cd_dev + 3 * (size_t)r.n_cd,
+                                                             out, r.lay.R);
+  KPM_CUDA(cudaGetLastError());
+  count_launches(2);
+  return KPM_OK;
+}
+
+int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2, cudaStream_t s,
+                    double *mu_r) {
   KPM_TRY(launch_finish(r, s));
+  if (r.per_vector && mu_r != nullptr) {
+    AssembleRArgs ar;
+    ar.sums_r = r.sums_r;
+    ar.sectors = r.tb.sectors;
+    ar.mu_r = mu_r;
+    ar.n_sectors = r.plan.n_sectors;
+    ar.K = r.K;
+    ar.R = r.lay.R;
+    const int64_t tot = (int64_t)r.plan.n_sectors * r.lay.R * r.K;
+    assemble_r_kernel<<<(int)std::min<int64_t>(4096, (tot + 255) / 256), 256, 0, s>>>(ar);
+    KPM_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
   AssembleArgs a;
   a.sums = r.sums;
   a.sectors = r.tb.sectors;
@@ -1254,7 +1430,8 @@ int launch_assemble(const MomentsRun &r, double *mu, double *mu_M, double *mu_M2
 }
 
 int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
-                int precision, MomentsJob *job) {
+                int precision, MomentsJob *job, const Knobs &knobs, int vectors,
+                bool per_vector) {
   KPM_TRY(validate_model(m));
   KPM_TRY(validate_sectors(m, n_sectors, n_up));
   job->n_sectors = n_sectors;
@@ -1264,16 +1441,19 @@ int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
   job->map_main.clear();
   job->map_side.clear();
   for (int i = 0; i < n_sectors; ++i) {
-    const bool small = precision == KPM_FP32 && kpm_sector_dim(m->n_sites, n_up[i]) < kFP32MinSectorDim;
+    const int64_t min_dim = knobs.side_min_dim >= 0 ? knobs.side_min_dim : kFP32MinSectorDim;
+    const bool small = precision == KPM_FP32 && kpm_sector_dim(m->n_sites, n_up[i]) < min_dim;
     (small ? job->nup_side : job->nup_main).push_back(n_up[i]);
     (small ? job->map_side : job->map_main).push_back(i);
   }
   job->has_main = !job->nup_main.empty();
   job->has_side = !job->nup_side.empty();
   if (job->has_main)
-    KPM_TRY(prepare_run(m, (int)job->nup_main.size(), job->nup_main.data(), K, R, precision, &job->main));
+    KPM_TRY(prepare_run(m, (int)job->nup_main.size(), job->nup_main.data(), K, R, precision,
+                        &job->main, knobs, vectors, per_vector));
   if (job->has_side) {
-    KPM_TRY(prepare_run(m, (int)job->nup_side.size(), job->nup_side.data(), K, R, KPM_FP64, &job->side));
+    KPM_TRY(prepare_run(m, (int)job->nup_side.size(), job->nup_side.data(), K, R, KPM_FP64,
+                        &job->side, knobs, vectors, per_vector));
     job->side.profile = false;
   }
   return KPM_OK;
@@ -1325,7 +1505,7 @@ struct ForkJoin {
 }  // namespace
 
 int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
-            cudaStream_t s, cudaStream_t side) {
+            cudaStream_t s, cudaStream_t side, double *mu_r) {
   const bool fork = side != nullptr && job.has_main && job.has_side;
   cudaStream_t ss = fork ? side : s;
   ForkJoin fj;
@@ -1340,24 +1520,27 @@ int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_
     if (!runs[k]) continue;
     KPM_TRY(launch_init(*runs[k], runs[k]->vA, seed, r0, st[k]));
     KPM_TRY(launch_step(*runs[k], runs[k]->vA, runs[k]->vB, 1, 0, st[k]));
+    KPM_TRY(launch_column_dots(*runs[k], runs[k]->vA, runs[k]->vB, 0, st[k]));
     xs[k] = runs[k]->vB;
     zs[k] = runs[k]->vA;
     if (!fork) {
       // serial: all steps of this run, then the next run
       for (int step = 1; step < S; ++step) {
         KPM_TRY(launch_step(*runs[k], xs[k], zs[k], 0, step, st[k]));
+        KPM_TRY(launch_column_dots(*runs[k], xs[k], zs[k], step, st[k]));
         std::swap(xs[k], zs[k]);
       }
-      KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k]));
+      KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k], mu_r));
     }
   }
   if (fork) {
     for (int step = 1; step < S; ++step)
       for (int k = 0; k < 2; ++k) {
         KPM_TRY(launch_step(*runs[k], xs[k], zs[k], 0, step, st[k]));
+        KPM_TRY(launch_column_dots(*runs[k], xs[k], zs[k], step, st[k]));
         std::swap(xs[k], zs[k]);
       }
-    for (int k = 0; k < 2; ++k) KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k]));
+    for (int k = 0; k < 2; ++k) KPM_TRY(launch_assemble(*runs[k], mu, mu_M, mu_M2, st[k], mu_r));
   }
   return KPM_OK;  // fj joins the side stream into s here
 }
@@ -1384,24 +1567,41 @@ int side_stream(cudaStream_t *out) {
 
 using namespace kpm;
 
-extern "C" size_t kpm_moments_workspace_size(const kpm_model *model, int32_t n_sectors,
-                                             const int32_t *n_up, int32_t n_moments, int32_t R,
-                                             int32_t precision) {
-  MomentsJob job;
-  if (prepare_job(model, n_sectors, n_up, n_moments, R, precision, &job) != KPM_OK) return 0;
-  return job_bytes(job);
+namespace kpm {
+
+// Options of a kpm_moments_ex call, checked; NULL means the defaults.
+int read_opts(const kpm_opts *o, kpm_opts *out) {
+  kpm_opts d{};
+  d.precision = KPM_FP64;
+  d.vectors = KPM_VECTORS_RADEMACHER;
+  if (o != nullptr) d = *o;
+  KPM_REQUIRE(d.precision == KPM_FP64 || d.precision == KPM_FP32, KPM_EINVAL, "precision %d",
+              d.precision);
+  KPM_REQUIRE(d.vectors == KPM_VECTORS_RADEMACHER || d.vectors == KPM_VECTORS_BASIS, KPM_EINVAL,
+              "vectors %d", d.vectors);
+  KPM_REQUIRE(d.ckpt_interval >= 0, KPM_EINVAL, "ckpt_interval %d", d.ckpt_interval);
+  *out = d;
+  return KPM_OK;
 }
 
-extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
-                           const double *a, const double *b, double eps, int32_t n_moments,
-                           int32_t R, uint64_t seed, uint64_t r0, int32_t precision, double *mu,
-                           double *mu_M, double *mu_M2, int32_t on_device, void *workspace,
-                           size_t ws_bytes, void *stream_ptr) {
-  clear_error();
+// The knobs for this problem: the autotuner's choice when asked for and
+// available, the defaults otherwise.
+Knobs knobs_for(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
+                const kpm_opts &o);
+
+int moments_impl(const kpm_model *model, int32_t n_sectors, const int32_t *n_up, const double *a,
+                 const double *b, double eps, int32_t n_moments, int32_t R, uint64_t seed,
+                 uint64_t r0, const kpm_opts &o, double *mu, double *mu_M, double *mu_M2,
+                 double *mu_r, int32_t on_device, void *workspace, size_t ws_bytes,
+                 void *stream_ptr) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_ptr);
   KPM_REQUIRE(mu != nullptr, KPM_EINVAL, "mu is NULL");
+  KPM_REQUIRE((mu_r != nullptr) == (o.per_vector != 0), KPM_EINVAL,
+              "mu_r must be given exactly when opts.per_vector is set");
   MomentsJob job;
-  KPM_TRY(prepare_job(model, n_sectors, n_up, n_moments, R, precision, &job));
+  KPM_TRY(prepare_job(model, n_sectors, n_up, n_moments, R, o.precision, &job,
+                      knobs_for(model, n_sectors, n_up, n_moments, R, o), o.vectors,
+                      o.per_vector != 0));
   std::vector<double> av, bv;
   if (a == nullptr || b == nullptr) {
     av.resize(n_sectors);
@@ -1412,27 +1612,32 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
     a = av.data();
     b = bv.data();
   }
-  const size_t out_bytes = align256((size_t)n_sectors * n_moments * sizeof(double));
-  const size_t need = job_bytes(job) + (on_device ? 0 : 3 * out_bytes);
+  const size_t SK = (size_t)n_sectors * n_moments;
+  const size_t out_bytes = align256(SK * sizeof(double));
+  const size_t r_bytes = mu_r ? align256(SK * R * sizeof(double)) : 0;
+  const size_t need = job_bytes(job) + (on_device ? 0 : 3 * out_bytes + r_bytes);
   Workspace ws;
   KPM_TRY(ws.acquire(workspace, ws_bytes, need, stream));
   Arena arena{reinterpret_cast<char *>(ws.ptr), ws.size, 0};
   KPM_TRY(setup_job(job, a, b, arena, stream));
-  double *dmu = mu, *dmuM = mu_M, *dmuM2 = mu_M2;
+  double *dmu = mu, *dmuM = mu_M, *dmuM2 = mu_M2, *dmur = mu_r;
   if (!on_device) {
-    dmu = arena.take<double>((size_t)n_sectors * n_moments);
-    dmuM = mu_M ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
-    dmuM2 = mu_M2 ? arena.take<double>((size_t)n_sectors * n_moments) : nullptr;
-    KPM_REQUIRE(dmu && (!mu_M || dmuM) && (!mu_M2 || dmuM2), KPM_ENOMEM, "workspace too small");
+    dmu = arena.take<double>(SK);
+    dmuM = mu_M ? arena.take<double>(SK) : nullptr;
+    dmuM2 = mu_M2 ? arena.take<double>(SK) : nullptr;
+    dmur = mu_r ? arena.take<double>(SK * R) : nullptr;
+    KPM_REQUIRE(dmu && (!mu_M || dmuM) && (!mu_M2 || dmuM2) && (!mu_r || dmur), KPM_ENOMEM,
+                "workspace too small");
   }
   cudaStream_t side = nullptr;
   if (job.has_main && job.has_side) KPM_TRY(side_stream(&side));
-  KPM_TRY(run_job(job, seed, r0, dmu, dmuM, dmuM2, stream, side));
-  const size_t nbytes = (size_t)n_sectors * n_moments * sizeof(double);
+  KPM_TRY(run_job(job, seed, r0, dmu, dmuM, dmuM2, stream, side, dmur));
+  const size_t nbytes = SK * sizeof(double);
   if (!on_device) {
     KPM_CUDA(cudaMemcpyAsync(mu, dmu, nbytes, cudaMemcpyDeviceToHost, stream));
     if (mu_M) KPM_CUDA(cudaMemcpyAsync(mu_M, dmuM, nbytes, cudaMemcpyDeviceToHost, stream));
     if (mu_M2) KPM_CUDA(cudaMemcpyAsync(mu_M2, dmuM2, nbytes, cudaMemcpyDeviceToHost, stream));
+    if (mu_r) KPM_CUDA(cudaMemcpyAsync(mu_r, dmur, nbytes * R, cudaMemcpyDeviceToHost, stream));
   }
   int flags[2] = {0, 0};
   if (job.has_main)
@@ -1445,4 +1650,53 @@ extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int3
     return KPM_EBOUNDS;
   }
   return KPM_OK;
+}
+
+}  // namespace kpm
+
+extern "C" size_t kpm_moments_workspace_size(const kpm_model *model, int32_t n_sectors,
+                                             const int32_t *n_up, int32_t n_moments, int32_t R,
+                                             int32_t precision) {
+  kpm_opts o{};
+  o.precision = precision;
+  return kpm_moments_ex_workspace_size(model, n_sectors, n_up, n_moments, R, &o);
+}
+
+extern "C" size_t kpm_moments_ex_workspace_size(const kpm_model *model, int32_t n_sectors,
+                                                const int32_t *n_up, int32_t n_moments,
+                                                int32_t R, const kpm_opts *opts) {
+  kpm_opts o;
+  if (read_opts(opts, &o) != KPM_OK) return 0;
+  MomentsJob job;
+  if (prepare_job(model, n_sectors, n_up, n_moments, R, o.precision, &job,
+                  knobs_for(model, n_sectors, n_up, n_moments, R, o), o.vectors,
+                  o.per_vector != 0) != KPM_OK)
+    return 0;
+  return job_bytes(job);
+}
+
+extern "C" int kpm_moments(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
+                           const double *a, const double *b, double eps, int32_t n_moments,
+                           int32_t R, uint64_t seed, uint64_t r0, int32_t precision, double *mu,
+                           double *mu_M, double *mu_M2, int32_t on_device, void *workspace,
+                           size_t ws_bytes, void *stream_ptr) {
+  clear_error();
+  kpm_opts o{};
+  o.precision = precision;
+  KPM_TRY(read_opts(&o, &o));
+  return moments_impl(model, n_sectors, n_up, a, b, eps, n_moments, R, seed, r0, o, mu, mu_M,
+                      mu_M2, nullptr, on_device, workspace, ws_bytes, stream_ptr);
+}
+
+extern "C" int kpm_moments_ex(const kpm_model *model, int32_t n_sectors, const int32_t *n_up,
+                              const double *a, const double *b, double eps, int32_t n_moments,
+                              int32_t R, uint64_t seed, uint64_t r0, const kpm_opts *opts,
+                              double *mu, double *mu_M, double *mu_M2, double *mu_r,
+                              int32_t on_device, void *workspace, size_t ws_bytes,
+                              void *stream_ptr) {
+  clear_error();
+  kpm_opts o;
+  KPM_TRY(read_opts(opts, &o));
+  return moments_impl(model, n_sectors, n_up, a, b, eps, n_moments, R, seed, r0, o, mu, mu_M,
+                      mu_M2, mu_r, on_device, workspace, ws_bytes, stream_ptr);
 }

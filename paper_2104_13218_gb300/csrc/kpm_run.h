@@ -5,6 +5,23 @@
 
 namespace kpm {
 
+// Choices of the moment loop that do not change its results beyond rounding
+// order: which step kernel, the tile size, the persistent grid, the row
+// mapping and which sectors of the FP32 form run in FP64.  Zero / negative
+// values select the library's defaults; kpm_autotune searches them.
+struct Knobs {
+  int lists = -1;            // neighbour-list kernel: -1 default, 0 off, 1 on (where it applies)
+  int64_t tile_states = 0;   // states per tile (0: default for the kernel)
+  int blocks_per_sm = 0;     // persistent grid: resident blocks per SM used (0: all that fit)
+  int two_state = -1;        // FP32 rows of 17..32 chunks as two states per warp: -1 default
+  int64_t side_min_dim = -1; // FP32 form: sectors below this dimension run in FP64 (-1: 1024)
+};
+
+// Random vectors of a run: Rademacher signs (Eq. E-2-7 with the sign
+// convention of the library) or, for complete-basis traces, unit vectors.
+constexpr int kVecRademacher = 0;
+constexpr int kVecBasis = 1;
+
 // Everything one forward run needs on the device.
 struct MomentsRun {
   Plan plan;
@@ -32,6 +49,18 @@ struct MomentsRun {
   // diagonal table hi / lo and group couplings hi / lo (lo only in FP32), and
   // two slots of per-tile sums (partials) used by alternate steps.
   void *coef[4] = {nullptr, nullptr, nullptr, nullptr};
+  Knobs knobs;
+  int vectors = kVecRademacher;
+  // Per-vector moments (optional): the rows are cut into chunks of one
+  // sector each; after every step a column kernel writes each chunk's
+  // per-vector dot products (cd_part) and a second kernel sums them per
+  // sector in chunk order into sums_r [S][n_sectors][R][2].
+  bool per_vector = false;
+  std::vector<int64_t> cd_chunks;  // host: (row_begin, row_end, sector) per chunk
+  const int64_t *cd_dev = nullptr; // device copy
+  int n_cd = 0;
+  double *cd_part = nullptr;       // [n_cd][R][2]
+  double *sums_r = nullptr;        // [S][n_sectors][R][2]
 };
 
 // The FP32 form stores sectors smaller than this in FP64: in a tiny sector the
@@ -49,19 +78,21 @@ struct MomentsJob {
   int n_sectors = 0, K = 0;
 };
 int prepare_job(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
-                int precision, MomentsJob *job);
+                int precision, MomentsJob *job, const Knobs &knobs = Knobs(),
+                int vectors = kVecRademacher, bool per_vector = false);
 size_t job_bytes(const MomentsJob &job);
 int setup_job(MomentsJob &job, const double *a, const double *b, Arena &arena, cudaStream_t s);
 // init + K/2 steps + assembly of both runs, all on stream s, or with a side
 // stream the FP64 side run on `side` (forked from and joined back into s).
 int run_job(MomentsJob &job, uint64_t seed, uint64_t r0, double *mu, double *mu_M, double *mu_M2,
-            cudaStream_t s, cudaStream_t side = nullptr);
+            cudaStream_t s, cudaStream_t side = nullptr, double *mu_r = nullptr);
 // The side stream of the current device (created on first use).
 int side_stream(cudaStream_t *out);
 
 // Builds the plan and the layout; no device work.
 int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, int R,
-                int precision, MomentsRun *run);
+                int precision, MomentsRun *run, const Knobs &knobs = Knobs(),
+                int vectors = kVecRademacher, bool per_vector = false);
 // Device bytes of the run's vectors (2), tables, partials, sums and counters.
 size_t run_bytes(const MomentsRun &run);
 // Carves the run's buffers from the arena and uploads tables (a, b per sector).
@@ -76,7 +107,13 @@ int launch_init(const MomentsRun &run, void *v0, uint64_t seed, uint64_t r0, cud
 int launch_step(const MomentsRun &run, const void *x, void *zy, int first, int step,
                 cudaStream_t s);
 // mu, mu_M, mu_M2 (device, may be NULL except mu) from sums; sets *flag on |mu| > 1+1e-6.
+// With per-vector moments also mu_r [caller sectors][R][K] (device).
 int launch_assemble(const MomentsRun &run, double *mu, double *mu_M, double *mu_M2,
-                    cudaStream_t s);
+                    cudaStream_t s, double *mu_r = nullptr);
+// Per-vector dot products of step `step` (x = v_n, y = v_{n+1}) into sums_r.
+int launch_column_dots(const MomentsRun &run, const void *x, const void *y, int step,
+                       cudaStream_t s);
+// Number of streaming multiprocessors of the current device.
+int sm_count();
 
 }  // namespace kpm

@@ -13,11 +13,16 @@
 // The array is a file-scope __device__ variable: every GPU that loads this
 // library holds kStaticScratchBytes for it until the process exits.  Its name
 // is only a host-side stand-in in host code, so the device address is looked
-// up once per device with cudaGetSymbolAddress (on the first call made while
-// that device is current) and then handed to the kernels.  All calls share
-// the array: the counters and flags that must start at zero are cleared at
-// the start of every call, and two calls whose work overlaps on the GPU (for
-// instance on two streams) race on it.
+// up with cudaGetSymbolAddress while the device is current and then handed to
+// the kernels.  The lookup is made once per device and CUDA context: the first
+// call on a device does it, and so does the first call after the context was
+// replaced (cudaDeviceReset destroys the primary context, and the array's
+// address in the new one need not be the old one).  The context is identified
+// by its unique id (cuCtxGetId, reached through the runtime's driver entry
+// points, so no driver library is linked).  All calls share the array: the
+// counters and flags that must start at zero are cleared at the start of every
+// call, and two calls whose work overlaps on the GPU (for instance on two
+// streams) race on it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,17 +40,51 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 void *g_static_ptr[kMaxDevices] = {};
+unsigned long long g_static_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current CUDA context (0 if there is none
+// or the driver cannot tell).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  }
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != 0 || ctx == nullptr ||
+      get_id(ctx, &id) != 0)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current device's context, looked
+// up on the first call in each device context.
 int static_scratch(void **out) {
   int dev = 0;
   KPM_CUDA(cudaGetDevice(&dev));
   KPM_REQUIRE(dev >= 0 && dev < kMaxDevices, KPM_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (g_static_ptr[dev] == nullptr) {
+  unsigned long long ctx = current_context_id();
+  if (g_static_ptr[dev] == nullptr || ctx == 0 || ctx != g_static_ctx[dev]) {
     void *p = nullptr;
     KPM_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
     g_static_ptr[dev] = p;
+    // the lookup creates the context if there was none yet
+    g_static_ctx[dev] = ctx != 0 ? ctx : current_context_id();
   }
   *out = g_static_ptr[dev];
   return KPM_OK;

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_function():
 
 def test_version_and_sector_dims():
     L = kpm.lib()
-    assert L.kpm_version() == 1
+    assert L.kpm_version() == 2
     assert L.kpm_sector_dim(34, 17) == 2333606220
     assert L.kpm_sector_dim(20, -1) == 1 << 20
     assert L.kpm_sector_dim(24, 12) == 2704156

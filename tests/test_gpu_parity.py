@@ -456,34 +456,106 @@ def test_j1j2_chain_gradient_full_size_matches_finite_differences():
         assert abs(theta.grad[p].item() - fd) <= 1e-4 * abs(fd), (p, theta.grad[p].item(), fd)
 
 
-def test_zeeman_field_by_shifted_rescaling_matches_ed():
-    """A Zeeman field h enters sector M as b -> b + h M (analysis.zeeman_shift): the GPU
-    thermodynamics of the ring N=10 with complete-basis-converged moments (large R) follows
-    the exact field-dependent curve within the statistical error."""
-    from paper_2104_13218_gb300 import analysis
+def test_zeeman_field_matches_oracle_and_ed():
+    """A Zeeman field h = g mu_B B (Eq. E-3-1-1) adds h M to the energies of sector M: the
+    library's thermodynamics in a field (kpm_thermo_ex) matches the oracle's quadrature
+    with every sector's shift b + h M written out, and, with complete-basis-converged
+    moments (large R), the exact field-dependent curve within the statistical error."""
     model = W.ring(10)
     bi, bj, J = model.arrays()
     n_up = W.all_sectors(10)
     h = 0.4
     a, b = _exact_bounds(model, n_up, 0.025)
-    # the same moments serve every field: only b moves
+    # the same moments serve every field
     mom = kpm.moments(model, n_up, 400, 200, 3, a=a, b=b)
     T = W.log_grid(0.5, 5.0, 20)
-    bh = analysis.zeeman_shift(b, n_up, 10, h)
-    secs = kpm.sector_set(10, n_up, a, bh)
-    got = kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, T)
+    secs = kpm.sector_set(10, n_up, a, b)
+    got = kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, T, field=h)
+    bh = np.array([b[i] + h * (k - 5) for i, k in enumerate(n_up)])
     ref_kpm = O.thermo_from_runs(10, n_up, [{"mu": m} for m in mom["mu"]], a, bh, T)
     ed = O.thermo_exact(10, bi, bj, J, T, field=h)
     for q in ("lnZ", "E", "C", "chi"):
-        # the quadrature of the same moments: parity with the oracle
         assert np.max(np.abs(got[q] - ref_kpm[q]) / np.maximum(1, np.abs(ref_kpm[q]))) < 1e-9, q
-        # and the physics: within the stochastic error of R = 200 vectors per sector
         assert np.max(np.abs(got[q] - ed[q]) / np.maximum(1, np.abs(ed[q]))) < 0.05, q
+    # the backward in a field against autograd through the oracle's quadrature
+    cot = {k: np.linspace(0.1, 1.0, len(T)) for k in ("lnZ", "E", "C", "chi")}
+    gb = kpm.thermo_backward(mom["mu"], mom["mu_M"], mom["mu_M2"], secs, T, cot, field=h)
+    tmu = [torch.tensor(m, requires_grad=True) for m in mom["mu"]]
+    Ms = [k - 5.0 for k in n_up]
+    dims, mult, _, _ = O.sector_weights(10, n_up)
+    out = O.thermo(tmu, [Ms[i] * tmu[i] for i in range(len(tmu))],
+                   [Ms[i] ** 2 * tmu[i] for i in range(len(tmu))], dims, mult, a, bh, T,
+                   torch_mod=torch)
+    L = sum((out[k] * torch.tensor(cot[k])).sum() for k in ("lnZ", "E", "C", "chi"))
+    L.backward()
+    total = gb["mu"] + np.array(Ms)[:, None] * gb["mu_M"] + (np.array(Ms) ** 2)[:, None] * gb["mu_M2"]
+    ref = np.array([t.grad.numpy() for t in tmu])
+    assert np.abs(total - ref).max() <= 1e-9 * np.abs(ref).max()
 
 
-def test_realisation_statistics():
-    """P realisations (Eq. E-3-1..E-3-3): their mean approaches the exact curve with a
-    spread that shrinks like 1/sqrt(R)."""
+def test_zeeman_field_with_mirrored_sectors():
+    """With mirrored sectors (M >= 0 only, M > 0 standing for +M and -M) the field splits each
+    pair into b + h M and b - h M with <M> contributions +M and -M; the result equals the
+    oracle's quadrature with both members listed as separate sectors sharing the moments."""
+    model = W.ring(10)
+    n_up = W.nonnegative_sectors(10)
+    mirror = [0 if k == 5 else 1 for k in n_up]
+    a, b = _exact_bounds(model, n_up, 0.025)
+    mom = kpm.moments(model, n_up, 120, 20, 8, a=a, b=b)
+    T = W.log_grid(0.3, 5.0, 15)
+    h = 0.7
+    got = kpm.thermo(mom["mu"], mom["mu_M"], mom["mu_M2"], kpm.sector_set(10, n_up, a, b, mirror), T,
+                     field=h)
+    # oracle: list the -M members explicitly with the same moments
+    n_all, mus, aa, bb = [], [], [], []
+    for i, k in enumerate(n_up):
+        for kk in ([k] if k == 5 else [k, 10 - k]):
+            n_all.append(kk)
+            mus.append({"mu": mom["mu"][i]})
+            aa.append(a[i])
+            bb.append(b[i] + h * (kk - 5))
+    ref = O.thermo_from_runs(10, n_all, mus, np.array(aa), np.array(bb), T)
+    for q in ("lnZ", "E", "C", "chi"):
+        assert np.max(np.abs(got[q] - ref[q]) / np.maximum(1, np.abs(ref[q]))) < 1e-9, q
+
+
+def test_realisation_statistics_match_oracle():
+    """P realisations (Eq. E-3-1..E-3-3) from one per-vector run (kpm_realisations): the
+    per-vector moments equal the oracle's single-vector runs, and the mean, variance and
+    systematic deviation equal the definitions evaluated on the oracle's thermodynamics of
+    each realisation."""
+    from paper_2104_13218_gb300 import analysis
+    model = W.ring(10)
+    bi, bj, J = model.arrays()
+    n_up = W.all_sectors(10)
+    a, b = _exact_bounds(model, n_up, 0.025)
+    T = W.log_grid(0.5, 5.0, 10)
+    ed = O.thermo_exact(10, bi, bj, J, T)
+    K, Rp, P, seed = 100, 3, 4, 5
+    mom = kpm.moments(model, n_up, K, Rp * P, seed, a=a, b=b, per_vector=True)
+    per = [[c_oracle.moments(10, bi, bj, J, k, a[i], b[i], K, 1, seed, r)["mu"]
+            for r in range(Rp * P)] for i, k in enumerate(n_up)]
+    per = np.array(per)  # [S, R, K]
+    assert np.max(np.abs(mom["mu_r"] - per)) <= 1e-10
+    assert np.max(np.abs(mom["mu_r"].mean(axis=1) - mom["mu"])) <= 1e-13
+    got = analysis.realisations(model, n_up, K, Rp, P, seed, a, b, T, exact=ed)
+    curves = []
+    for p in range(P):
+        runs = [{"mu": per[i, p * Rp:(p + 1) * Rp].mean(axis=0)} for i in range(len(n_up))]
+        curves.append(O.thermo_from_runs(10, n_up, runs, a, b, T))
+    for q in ("lnZ", "E", "C", "chi"):
+        allq = np.array([c[q] for c in curves])
+        mean = allq.mean(axis=0)
+        var = (allq ** 2).mean(axis=0) - mean ** 2
+        sc = max(1.0, np.abs(allq).max())
+        assert np.max(np.abs(got[q]["all"] - allq)) <= 1e-9 * sc, q
+        assert np.max(np.abs(got[q]["mean"] - mean)) <= 1e-9 * sc, q
+        assert np.max(np.abs(got[q]["var"] - var)) <= 1e-9 * sc * sc, q
+        assert np.max(np.abs(got[q]["dev"] - np.abs(mean - ed[q]))) <= 1e-9 * sc, q
+
+
+def test_realisation_spread_shrinks_with_R():
+    """The realisation spread falls like 1/sqrt(R) (Sec. 3.1.1), the mean approaches ED."""
     from paper_2104_13218_gb300 import analysis
     model = W.ring(10)
     bi, bj, J = model.arrays()
@@ -493,9 +565,7 @@ def test_realisation_statistics():
     ed = O.thermo_exact(10, bi, bj, J, T)
     r4 = analysis.realisations(model, n_up, 200, 4, 12, 5, a, b, T, exact=ed)
     r16 = analysis.realisations(model, n_up, 200, 16, 12, 5, a, b, T, exact=ed)
-    # spread shrinks with R (dO ~ 1/sqrt(R): a factor 2 from R = 4 to 16, checked loosely)
     assert np.mean(np.sqrt(r16["C"]["var"])) < 0.8 * np.mean(np.sqrt(r4["C"]["var"]))
-    # the mean is consistent with the exact curve within a few standard errors
     sem = np.sqrt(r16["C"]["var"] / 12) + 1e-3
     assert np.all(r16["C"]["dev"] < 6 * sem + 0.02)
     assert r4["C"]["all"].shape == (12, len(T))

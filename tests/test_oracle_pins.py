@@ -464,23 +464,6 @@ def test_jackson_kernel_turns_the_ghost_dip_into_a_peak(ladder14):
     assert np.abs(dev[500, "jackson"][high]).max() < 0.1 * np.abs(dev[100, "jackson"][high]).max()
 
 
-def test_order_eps_and_quadrature_points(ladder14):
-    """Sec. 3.1.2 with exact traces: a higher order N_deg pushes the ghost dip to
-    lower T; eps > 0 makes C worse (eps = 0 is best, with eps ~ 1e-6 marginally
-    shallower); N~ below N_deg breaks the quadrature while N~ >= N_deg works."""
-    T = ladder14["T"]
-    dev = ladder14["deviation"]
-    t_min = [T[np.argmin(dev(K))] for K in (50, 100, 200, 400)]
-    assert all(t1 < t0 for t0, t1 in zip(t_min, t_min[1:]))
-    d0 = np.abs(dev(100)).max()
-    for eps in (0.01, 0.05):
-        assert np.abs(dev(100, eps=eps)).max() > 10 * d0
-    assert dev(100, eps=1e-6).min() > dev(100).min()
-    assert np.abs(dev(100, n_quad=50)).max() > 100 * d0
-    for nq in (150, 200):
-        assert np.abs(dev(100, n_quad=nq)).max() < 2 * d0
-
-
 def test_statistical_error_of_C_scales_as_inverse_sqrt_R():
     """Statistical deviations (Sec. 3.1.1, Eq. E-3-1 .. E-3-3): over independent
     realisations the spread of the estimated heat capacity falls like 1/sqrt(R)
