@@ -62,6 +62,14 @@ def parse_args():
     p.add_argument("--large-steps", type=int, default=20,
                    help="Chebyshev steps per timed block of the large workloads")
     p.add_argument("--large-reps", type=int, default=3)
+    p.add_argument("--large-workloads", default="ring34_m0,j1j2sq24_full",
+                   help="comma-separated workloads of the large blocks")
+    p.add_argument("--only-large", action="store_true",
+                   help="time only the large blocks (print one line per workload)")
+    p.add_argument("--no-gradient", action="store_true",
+                   help="skip the forward + adjoint pass of the gradient workload")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip the autotuner runs reported beside the workloads")
     p.add_argument("--tuned", action="store_true",
                    help="autotune the headline workload first and time the tuned schedule")
     return p.parse_args()
@@ -301,14 +309,22 @@ def run_ours(args):
         return ms, prof, prof[2] - launches0, clk
 
     hbm_peak, peak_kind = peaks()
+    if args.only_large:
+        for key in args.large_workloads.split(","):
+            res = large_block(args, key, timed, hbm_peak, peak_kind)
+            if rank == 0:
+                print(json.dumps(res), flush=True)
+        return 0
     tune_info = None
-    if args.tuned:
+    if args.tuned or not args.no_autotune:
         bnd0 = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=args.lanczos_iters,
                           tol=args.lanczos_tol, seed=w.seed)
         t = kpm.autotune(w.model, w.n_up, bnd0["a"], bnd0["b"], w.R, precision=precision,
                          trial_steps=16)
         tune_info = {"default_ms_per_step": t["default_ms"], "tuned_ms_per_step": t["best_ms"],
-                     "choice": t["report"].splitlines()[0]}
+                     "gain": t["default_ms"] / t["best_ms"] if t["best_ms"] > 0 else None,
+                     "choice": t["report"].splitlines()[0],
+                     "timed_run_uses": "tuned schedule" if args.tuned else "default schedule"}
     step, last = make(precision)
     ms, prof, launches, clk = timed(step, args.steps, args.warmup, profile=True, clocks=True)
     value = units * world * args.steps / (ms / 1e3)
@@ -393,7 +409,9 @@ def run_ours(args):
         line["autotune"] = tune_info
     if not args.no_large:
         line["workloads"] = {key: large_block(args, key, timed, hbm_peak, peak_kind)
-                             for key in ("ring34_m0", "j1j2sq24_full")}
+                             for key in args.large_workloads.split(",")}
+    if not args.no_gradient:
+        line["gradient"] = gradient_block(args, timed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import c_oracle
         c_oracle.build()
@@ -410,7 +428,8 @@ def run_ours(args):
 # Fixed rescaling of the two largest workloads (their spectra lie inside): the ring
 # N = 34 S^z = 0 sector in [-15.1, 8.5], the 4 x 6 J1-J2 torus in [-20, 18].  The same
 # values produce the stored oracle moments the full-size tests compare against.
-LARGE = {"ring34_m0": (13.0, -3.5), "j1j2sq24_full": (20.0, 0.0)}
+LARGE = {"ring34_m0": (13.0, -3.5), "j1j2sq24_full": (20.0, 0.0),
+         "ring30_m0": (11.5, -3.0), "j1j2sq20_full": (17.0, 0.0)}
 
 
 def large_block(args, key, timed, hbm_peak, peak_kind):
@@ -461,6 +480,13 @@ def large_block(args, key, timed, hbm_peak, peak_kind):
            "clocks": clk, "gpu_launches": launches}
     del ws, out
     torch.cuda.empty_cache()
+    if not args.no_autotune:
+        t = kpm.autotune(w.model, w.n_up, [a] * S, [b] * S, w.R, precision="fp32", trial_steps=4)
+        res["autotune"] = {"default_ms_per_step": t["default_ms"], "tuned_ms_per_step": t["best_ms"],
+                           "gain": t["default_ms"] / t["best_ms"] if t["best_ms"] > 0 else None,
+                           "choice": t["report"].splitlines()[0],
+                           "note": "per matrix-vector product of a 5-product trial run, incl. "
+                                   "random vectors and assembly"}
     # end to end through the public API with host outputs
     t0 = time.perf_counter()
     kpm.moments(w.model, w.n_up, K, w.R, w.seed, a=[a] * S, b=[b] * S, precision="fp32",
@@ -500,6 +526,45 @@ def large_block(args, key, timed, hbm_peak, peak_kind):
     return res
 
 
+def gradient_block(args, timed):
+    """One forward + adjoint pass of the gradient workload (J1-J2 chain N = 24, sectors
+    M = 0..12 with M > 0 mirrored, R = 32, K = 1000, FP64): loss = mean squared error of
+    chi(T) on the 50-point grid against the curve at (J1, J2) = (1, 0.3), gradient at
+    (1, 0.2) through kpm_thermo_backward and kpm_moments_backward (checkpoints every 32)."""
+    import torch
+
+    import paper_2104_13218_gb300 as kpm
+
+    w = W.workload("j1j2chain24_grad")
+    bnd = kpm.bounds(w.model, w.n_up, eps=w.eps, max_iter=120, tol=1e-8, seed=w.seed)
+    spec = dict(model=w.model, n_up=w.n_up, mirror=w.mirror, a=np.maximum(bnd["a"], 0.5),
+                b=bnd["b"], K=w.K, R=w.R, seed=w.seed, T=w.T, kernel="none", ckpt_interval=32)
+    with torch.no_grad():
+        target = kpm.chebyshev_thermo(torch.tensor([1.0, 0.3], dtype=torch.float64), spec)[3]
+    keep = {}
+
+    def forward():
+        th = torch.tensor([1.0, 0.2], dtype=torch.float64)
+        with torch.no_grad():
+            keep["loss"] = float(((kpm.chebyshev_thermo(th, spec)[3] - target) ** 2).mean())
+
+    def forward_backward():
+        th = torch.tensor([1.0, 0.2], dtype=torch.float64, requires_grad=True)
+        loss = ((kpm.chebyshev_thermo(th, spec)[3] - target) ** 2).mean()
+        loss.backward()
+        keep["grad"] = [float(g) for g in th.grad]
+
+    ms_f, _, _, _ = timed(forward, 1, 0)
+    ms_fb, _, launches, clk = timed(forward_backward, 1, 0)
+    D = sum(kpm_dim(w.model.n_sites, k) for k in w.n_up)
+    units = D * w.R * w.steps
+    return {"workload": w.key, "note": w.note, "ms_forward": ms_f, "ms_forward_backward": ms_fb,
+            "ms_backward": ms_fb - ms_f, "backward_over_forward": (ms_fb - ms_f) / ms_f,
+            "forward_value": units / (ms_f / 1e3), "unit": UNIT, "loss": keep.get("loss"),
+            "grad": keep.get("grad"), "clocks": clk, "gpu_launches": launches,
+            "dtype": "f64", "ckpt_interval": 32}
+
+
 def ctypes_read(L):
     import ctypes
     ms = ctypes.c_double(0)
@@ -513,7 +578,9 @@ def step_kernel_name(w, precision):
     """Which step kernel the library picks for this workload: the neighbour-list
     kernel for cooperative row layouts (2+ lanes per state, 1 or 2 chunks per
     lane) with at most 4 distinct couplings, 255 bonds and a diagonal table of
-    at most 4096 entries; the matrix-free kernel otherwise."""
+    at most 4096 entries; the hi-block kernel for one-lane rows of sector runs
+    with at most 4 distinct couplings and 64 bonds; the matrix-free kernel
+    otherwise."""
     vw = 4 if precision == "fp32" else 2
     chunks = -(-w.R // vw)
     cpl = -(-chunks // 32)
@@ -525,6 +592,9 @@ def step_kernel_name(w, precision):
         table *= sum(1 for J in w.model.J if J == v) + 1
     grouped = len(vals) <= 4 and table <= 4096 and w.model.n_bonds > 0
     lists = G >= 2 and cpl <= 2 and grouped and w.model.n_bonds <= 255
+    block = G == 1 and grouped and w.model.n_bonds <= 64 and all(k >= 0 for k in w.n_up)
+    if block:
+        return "cheb_block_kernel"
     return "cheb_step_list_kernel" if lists else "cheb_step_kernel"
 
 

@@ -196,7 +196,18 @@ def workload(key: str) -> Workload:
         return Workload(key, ring(34), [17], R=4, K=2000, seed=5, eps=0.025,
                         T=log_grid(0.02, 10.0, 200), precisions=("fp32",),
                         note="ring N=34, S^z=0 sector (dim 2333606220), R=4, 2000 moments")
+    # scaled cases of the two largest workloads, small enough for detailed profiles
+    # (a few GB on the device, still far larger than L2)
+    if key == "ring30_m0":
+        return Workload(key, ring(30), [15], R=4, K=2000, seed=5, eps=0.025,
+                        T=log_grid(0.02, 10.0, 200), precisions=("fp32",),
+                        note="ring N=30, S^z=0 sector (dim 155117520), R=4, 2000 moments")
+    if key == "j1j2sq20_full":
+        return Workload(key, j1j2_square(4, 5, 1.0, 0.5), [FULL_SPACE], R=64, K=2000, seed=3,
+                        eps=0.025, T=log_grid(0.02, 10.0, 200), precisions=("fp32", "fp64"),
+                        note="J1-J2 4x5 torus, full 2^20 space, R=64, 2000 moments")
     raise KeyError(key)
 
 
-WORKLOADS = ("ring10_full", "ring20_sectors", "j1j2sq24_full", "j1j2chain24_grad", "ring34_m0")
+WORKLOADS = ("ring10_full", "ring20_sectors", "j1j2sq24_full", "j1j2chain24_grad", "ring34_m0",
+             "ring30_m0", "j1j2sq20_full")

@@ -100,8 +100,9 @@ int64_t binom(int n, int k);
 int validate_model(const kpm_model *m);
 int validate_sectors(const kpm_model *m, int n_sectors, const int32_t *n_up);
 // Builds tables and tiles; tile_states = states per tile (a power of two).
+// L_split > 0 sets the low/high split of the rank tables (default N/2).
 int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t tile_states,
-               Plan *plan);
+               Plan *plan, int L_split = 0);
 // States per tile for a layout with gpw states per warp and total_rows rows.
 int64_t choose_tile_states(int gpw, int64_t total_rows);
 // States per tile of the list kernel, whose tiles are taken by single warps.

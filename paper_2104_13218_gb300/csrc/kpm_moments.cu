@@ -465,6 +465,10 @@ __host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
 #define KPM_LIST_MIN_BLOCKS 3
 #endif
 
+// Shared memory budget (KB) of the hi-block kernel's staged block and rank table.
+#ifndef KPM_BLOCK_SMEM_KB
+#define KPM_BLOCK_SMEM_KB 48
+#endif
 // Padding unit of each group's list entries: the FP32 gather batch, 1 in FP64.
 inline int list_pad(int precision, int cpl) {
   return precision == KPM_FP32 ? list_batch(true, cpl) : 1;
@@ -544,14 +548,6 @@ inline size_t list_smem_bytes(int gpw, int stride) {
   return (size_t)kWarps * 2 * gpw * stride * sizeof(uint32_t);
 }
 
-// Coefficients of H' for the list kernel, per sector and per kind of step
-// (first: A = 1/a, later: A = 2/a), computed on the host once per run:
-// the diagonal A (d - b) for every combination of flip counts (table_size
-// entries) and A J_g / 2 for every coupling group, each as hi (+ lo in FP32).
-struct CoefDev {
-  const void *diag_hi, *diag_lo;  // [n_sectors][2][table_size] of T
-  const void *grp_hi, *grp_lo;    // [n_sectors][2][kMaxGroups] of T
-};
 
 // One Chebyshev step driven by the neighbour lists (cooperative layouts with
 // grouped couplings).  Warps work independently: each takes small tiles from
@@ -1011,6 +1007,7 @@ void *pick_list(int precision, int cpl, bool full) {
 }
 
 void *pick_kernel(const MomentsRun &r) {
+  if (r.block_L > 0) return block_kernel_ptr(r.precision);
   if (r.list_stride > 0) return pick_list(r.precision, r.lay.cpl, r.plan.any_full);
   return pick_step(r.precision, r.lay.cpl, r.plan.any_full);
 }
@@ -1037,6 +1034,7 @@ void *pick_step(int precision, int cpl, bool full) {
 size_t step_smem(const MomentsRun &r) {
   // matrix-free kernel: diagonal table, hi + lo floats (FP32) or one double
   // (FP64) per entry; list kernel: two list buffers of gpw states per warp
+  if (r.block_L > 0) return block_smem_bytes(r);
   if (r.list_stride > 0) return list_smem_bytes(r.lay.gpw, r.list_stride);
   return (size_t)r.bonds.table_size * 8;
 }
@@ -1099,6 +1097,25 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
     }
     if (list_smem_bytes(run->lay.gpw, stride) <= kMaxListSmem) run->list_stride = stride;
   }
+  // hi-block kernel: one lane per state (one 16-byte chunk per row), sectors
+  // only, grouped couplings; the low split L is the largest at which the
+  // largest block (C(L, L/2) rows) and the 16-bit lo_rank table fit 48 KB of
+  // shared memory
+  run->block_L = 0;
+  if (knobs.block != 0 && run->lay.G == 1 && run->lay.cpl == 1 && run->list_stride == 0 &&
+      run->bonds.n_groups > 0 && m->n_bonds <= kBlockMaxBonds) {
+    bool sectors_only = true;
+    for (int s2 = 0; s2 < n_sectors; ++s2) sectors_only &= n_up[s2] >= 0;
+    int Lb = 0;
+    for (int Lc = std::min(m->n_sites / 2, 16); Lc >= 1; --Lc) {
+      const size_t bytes = (((size_t)2 << Lc) + 15) / 16 * 16 + (size_t)binom(Lc, Lc / 2) * 16;
+      if (bytes <= KPM_BLOCK_SMEM_KB * 1024 && m->n_sites - Lc <= 22) {
+        Lb = Lc;
+        break;
+      }
+    }
+    if (sectors_only && Lb > 0) run->block_L = Lb;
+  }
   int64_t ts = run->list_stride > 0 ? list_tile_states(run->lay.gpw, rows)
                                     : choose_tile_states(run->lay.gpw, rows);
   if (knobs.tile_states > 0) {
@@ -1109,7 +1126,46 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
     if (run->list_stride > 0)
       ts = std::max<int64_t>(ts, (rows + KPM_LIST_MAX_TILES - 1) / KPM_LIST_MAX_TILES);
   }
-  KPM_TRY(build_plan(m, n_sectors, n_up, ts, &run->plan));
+  KPM_TRY(build_plan(m, n_sectors, n_up, ts, &run->plan, run->block_L));
+  if (run->block_L > 0) {
+    // split the bonds by where their sites lie, each kind sorted by coupling group
+    BlockBondsDev &bb = run->bb;
+    bb = BlockBondsDev{};
+    const int L = run->block_L;
+    bb.L = L;
+    bb.n_groups = run->bonds.n_groups;
+    for (int g = 0; g < kMaxGroups; ++g) bb.tstride[g] = run->bonds.tstride[g];
+    int nl = 0, nh = 0, nx = 0;
+    for (int g = 0; g < run->bonds.n_groups; ++g) {
+      bb.low_gs[g] = nl;
+      bb.high_gs[g] = nh;
+      bb.cross_gs[g] = nx;
+      for (int k = run->bonds.gstart[g]; k < run->bonds.gstart[g + 1]; ++k) {
+        const int b = run->bonds.order[k];
+        const int i = std::min(m->bi[b], m->bj[b]), j = std::max(m->bi[b], m->bj[b]);
+        if (j < L) {
+          bb.low_mask[nl++] = (1u << i) | (1u << j);
+        } else if (i >= L) {
+          bb.high_mask[nh++] = (1u << (i - L)) | (1u << (j - L));
+        } else {
+          bb.cross_lo[nx] = (uint8_t)i;
+          bb.cross_hi[nx] = (uint8_t)(j - L);
+          ++nx;
+        }
+      }
+    }
+    for (int g = run->bonds.n_groups; g <= kMaxGroups; ++g) {
+      bb.low_gs[g] = nl;
+      bb.high_gs[g] = nh;
+      bb.cross_gs[g] = nx;
+    }
+    run->max_block = 0;
+    for (int s2 = 0; s2 < n_sectors; ++s2) {
+      const int k = n_up[s2];
+      for (int c = std::max(0, k - (m->n_sites - L)); c <= std::min(L, k); ++c)
+        run->max_block = std::max<int64_t>(run->max_block, binom(L, c));
+    }
+  }
   if (per_vector) {
     // chunks of rows, each inside one sector, for the per-vector column sums
     const int64_t ch = std::min<int64_t>(65536, std::max<int64_t>(256, run->plan.total_rows / 2048));
@@ -1149,9 +1205,16 @@ size_t run_bytes(const MomentsRun &r) {
   size_t coef = 0;
   if (lists)
     for (int w = 0; w < 4; ++w) coef += coef_bytes(r, w);
+  if (r.block_L > 0)
+    for (int w = 0; w < 4; ++w) coef += coef_bytes(r, w);
+  const size_t nblk = r.plan.hb_hi.size();
+  const size_t slots = std::max(r.plan.tiles.size(), r.block_L > 0 ? nblk : 0);
   return 2 * r.vec_bytes + tables_bytes(r.plan) + coef +
+         (r.block_L > 0 ? align256(nblk * sizeof(int32_t)) +
+                              align256((size_t)2 * r.plan.n_sectors * sizeof(int32_t))
+                        : 0) +
          align256((size_t)r.plan.total_rows * r.list_stride * sizeof(uint32_t)) +
-         align256((lists ? 2 : 1) * r.plan.tiles.size() * r.NQ * sizeof(double)) +
+         align256((lists ? 2 : 1) * slots * r.NQ * sizeof(double)) +
          align256((size_t)r.S * r.plan.n_sectors * r.NQ * sizeof(double)) +
          align256((size_t)2 * r.S * sizeof(int)) + 256 +
          (r.per_vector ? align256(r.cd_chunks.size() * sizeof(int64_t)) +
@@ -1223,7 +1286,8 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
               const int *out_index) {
   r.vA = arena.take<char>(r.vec_bytes);
   r.vB = arena.take<char>(r.vec_bytes);
-  const size_t n_partials = (r.list_stride > 0 ? 2 : 1) * r.plan.tiles.size() * r.NQ;
+  const size_t slots = std::max(r.plan.tiles.size(), r.block_L > 0 ? r.plan.hb_hi.size() : 0);
+  const size_t n_partials = (r.list_stride > 0 ? 2 : 1) * slots * r.NQ;
   r.partials = arena.take<double>(std::max<size_t>(1, n_partials));
   r.sums = arena.take<double>((size_t)r.S * r.plan.n_sectors * r.NQ);
   r.counters = arena.take<int>((size_t)2 * r.S);
@@ -1265,6 +1329,30 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     count_launches(1);
     KPM_TRY(upload_coefficients(r, sec, arena, s));
   }
+  if (r.block_L > 0) {
+    // sector of every hi-block, and each sector's block range (for the sums)
+    const size_t nblk = r.plan.hb_hi.size();
+    std::vector<int32_t> bsec(nblk), ranges(2 * (size_t)r.plan.n_sectors);
+    for (int i = 0; i < r.plan.n_sectors; ++i) {
+      const int32_t b0 = r.plan.hb_begin[i];
+      const int32_t b1 = i + 1 < r.plan.n_sectors ? r.plan.hb_begin[i + 1] : (int32_t)nblk;
+      for (int32_t b = b0; b < b1; ++b) bsec[b] = i;
+      ranges[i] = b0;
+      ranges[r.plan.n_sectors + i] = b1;
+    }
+    int32_t *dsec = arena.take<int32_t>(nblk);
+    r.blk_ranges = arena.take<int32_t>(ranges.size());
+    KPM_REQUIRE(dsec && r.blk_ranges, KPM_ENOMEM, "workspace too small for the hi-block tables");
+    KPM_CUDA(cudaMemcpyAsync(dsec, bsec.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    KPM_CUDA(cudaMemcpyAsync(r.blk_ranges, ranges.data(), ranges.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
+    r.blk_sector = dsec;
+    r.tbb = r.tb;
+    r.tbb.tile_begin = r.blk_ranges;
+    r.tbb.tile_end = r.blk_ranges + r.plan.n_sectors;
+    r.tbb.n_tiles = (int32_t)nblk;
+    KPM_TRY(upload_coefficients(r, sec, arena, s));
+  }
   if (r.per_vector) {
     int64_t *cd = arena.take<int64_t>(r.cd_chunks.size());
     r.cd_part = arena.take<double>((size_t)r.n_cd * r.lay.R * 2);
@@ -1279,10 +1367,13 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
   KPM_CUDA(cudaMemsetAsync(r.flag, 0, sizeof(int), s));
   void *fn = pick_kernel(r);
   int per_sm = 0;
+  if (r.block_L > 0 && step_smem(r) > 48 * 1024)
+    KPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(r)));
   KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, step_smem(r)));
   per_sm = std::max(per_sm, 1);
   if (r.knobs.blocks_per_sm > 0) per_sm = std::min(per_sm, r.knobs.blocks_per_sm);
-  r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), (int64_t)r.plan.tiles.size());
+  const int64_t items = r.block_L > 0 ? (int64_t)r.plan.hb_hi.size() : (int64_t)r.plan.tiles.size();
+  r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), items);
   r.grid = std::max(r.grid, 1);
   return KPM_OK;
 }
@@ -1335,6 +1426,26 @@ int launch_step(const MomentsRun &r, const void *x, void *zy, int first, int ste
       a.prev_partials = r.partials + ((step - 1) & 1) * slot;
       a.prev_sums = r.sums + (size_t)(step - 1) * r.plan.n_sectors * r.NQ;
     }
+  }
+  if (r.block_L > 0) {
+    // the hi-block kernel writes one slot per block; the sums follow in block order
+    cudaEvent_t b0 = nullptr, b1 = nullptr;
+    const bool bprof = r.profile && profiling();
+    if (bprof) {
+      KPM_CUDA(cudaEventCreate(&b0));
+      KPM_CUDA(cudaEventCreate(&b1));
+      KPM_CUDA(cudaEventRecord(b0, s));
+    }
+    KPM_TRY(launch_block_step(r, x, zy, first, r.partials, a.queue, cf, s));
+    count_launches(1);
+    if (bprof) {
+      KPM_CUDA(cudaEventRecord(b1, s));
+      profile_push(b0, b1);
+    }
+    reduce_tile_sums_kernel<2><<<r.plan.n_sectors, kThreads, 0, s>>>(r.partials, r.tbb, a.sums);
+    KPM_CUDA(cudaGetLastError());
+    count_launches(1);
+    return KPM_OK;
   }
   void *fn = pick_kernel(r);
   const uint32_t *lists = r.lists;

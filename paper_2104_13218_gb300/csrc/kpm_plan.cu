@@ -94,7 +94,7 @@ int64_t list_tile_states(int gpw, int64_t total_rows) {
 }
 
 int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t tile_states,
-               Plan *p) {
+               Plan *p, int L_split) {
   KPM_TRY(validate_model(m));
   KPM_TRY(validate_sectors(m, n_sectors, n_up));
   KPM_REQUIRE(tile_states >= 1, KPM_EINVAL, "tile_states < 1");
@@ -103,8 +103,9 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
     KPM_REQUIRE(n_up[s] >= 0 || N <= 32, KPM_EINVAL,
                 "the full 2^N space is limited to N <= 32 (ranks are 32-bit); use sectors");
   p->N = N;
-  p->L = N / 2;
+  p->L = (L_split > 0 && L_split <= N) ? L_split : N / 2;
   p->H = N - p->L;
+  KPM_REQUIRE(p->H <= 24, KPM_EINVAL, "high part of %d bits: rank tables too large", p->H);
   p->n_sectors = n_sectors;
   p->n_up.assign(n_up, n_up + n_sectors);
   p->dim.resize(n_sectors);
@@ -150,16 +151,19 @@ int build_plan(const kpm_model *m, int n_sectors, const int32_t *n_up, int64_t t
     p->lo_list.resize(nlo);
     std::vector<uint32_t> fill(p->lo_start.begin(), p->lo_start.end());
     for (uint32_t lo = 0; lo < nlo; ++lo) p->lo_list[fill[__builtin_popcount(lo)]++] = lo;
-    // high part given c set bits below it
+    // high part given c set bits below it: the terms C(L + q, j) of its set
+    // bits q, the j-th set bit overall; built from the entry without the top
+    // bit, so each entry costs one addition
     p->hi_rank.resize((size_t)(L + 1) * nhi);
-    for (int c = 0; c <= L; ++c)
-      for (uint32_t hi = 0; hi < nhi; ++hi) {
-        uint64_t r = 0;
-        int j = c;
-        for (int q = 0; q < H; ++q)
-          if ((hi >> q) & 1u) r += (uint64_t)C[L + q][++j];
-        p->hi_rank[(size_t)c * nhi + hi] = (uint32_t)r;
+    for (int c = 0; c <= L; ++c) {
+      uint32_t *row = p->hi_rank.data() + (size_t)c * nhi;
+      row[0] = 0;
+      for (uint32_t hi = 1; hi < nhi; ++hi) {
+        const int top = 31 - __builtin_clz(hi);
+        const uint32_t rest = hi & ~(1u << top);
+        row[hi] = row[rest] + (uint32_t)C[L + top][c + __builtin_popcount(hi)];
       }
+    }
     // hi-blocks of every sector in increasing order of the high pattern
     for (int s = 0; s < n_sectors; ++s) {
       p->hb_begin[s] = (int32_t)p->hb_hi.size();

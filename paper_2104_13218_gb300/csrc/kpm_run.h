@@ -15,6 +15,32 @@ struct Knobs {
   int blocks_per_sm = 0;     // persistent grid: resident blocks per SM used (0: all that fit)
   int two_state = -1;        // FP32 rows of 17..32 chunks as two states per warp: -1 default
   int64_t side_min_dim = -1; // FP32 form: sectors below this dimension run in FP64 (-1: 1024)
+  int block = -1;            // hi-block kernel for one-lane sector layouts: -1 default, 0 off
+};
+
+// Coefficients of H' per sector and kind of step (first: A = 1/a, later:
+// A = 2/a), computed on the host once per run: the diagonal A (d - b) for every
+// combination of anti-aligned bond counts per coupling group, and A J_g / 2 for
+// every group, each as hi (+ lo in FP32).
+struct CoefDev {
+  const void *diag_hi, *diag_lo;  // [n_sectors][2][table_size] of T
+  const void *grp_hi, *grp_lo;    // [n_sectors][2][kMaxGroups] of T
+};
+
+// Bonds of the hi-block kernel, split by where their sites lie relative to the
+// low bits (L): low bonds (both sites below L, masks on the low bits), high
+// bonds (both at or above L, masks on the high bits) and cross bonds (one of
+// each: low bit position, high bit position).  Each list is sorted by
+// coupling group; *_gs[g] .. *_gs[g+1] are the bonds of group g.
+constexpr int kBlockMaxBonds = 64;
+struct BlockBondsDev {
+  int32_t L;
+  int32_t n_groups;
+  int32_t tstride[kMaxGroups];
+  int32_t low_gs[kMaxGroups + 1], high_gs[kMaxGroups + 1], cross_gs[kMaxGroups + 1];
+  uint32_t low_mask[kBlockMaxBonds];
+  uint32_t high_mask[kBlockMaxBonds];
+  uint8_t cross_lo[kBlockMaxBonds], cross_hi[kBlockMaxBonds];
 };
 
 // Random vectors of a run: Rademacher signs (Eq. E-2-7 with the sign
@@ -50,6 +76,15 @@ struct MomentsRun {
   // two slots of per-tile sums (partials) used by alternate steps.
   void *coef[4] = {nullptr, nullptr, nullptr, nullptr};
   Knobs knobs;
+  // Hi-block kernel (one lane per state, sector runs): one work item per
+  // hi-block, whose rows are staged in shared memory; block_L > 0 selects it
+  // and is the low split of the rank tables.
+  int block_L = 0;
+  int64_t max_block = 0;           // states of the largest hi-block
+  BlockBondsDev bb{};
+  const int32_t *blk_sector = nullptr;  // [n_blocks] sector of each hi-block
+  TablesDev tbb{};                 // tables whose "tiles" are the hi-blocks (for the sums)
+  int32_t *blk_ranges = nullptr;   // [2][n_sectors]: first / end hi-block of each sector
   int vectors = kVecRademacher;
   // Per-vector moments (optional): the rows are cut into chunks of one
   // sector each; after every step a column kernel writes each chunk's
@@ -115,5 +150,10 @@ int launch_column_dots(const MomentsRun &run, const void *x, const void *y, int 
                        cudaStream_t s);
 // Number of streaming multiprocessors of the current device.
 int sm_count();
+// The hi-block kernel (kpm_block.cu): shared memory, launch of one step.
+size_t block_smem_bytes(const MomentsRun &run);
+int launch_block_step(const MomentsRun &run, const void *x, void *zy, int first, double *partials,
+                      int *queue, CoefDev cf, cudaStream_t s);
+void *block_kernel_ptr(int precision);
 
 }  // namespace kpm

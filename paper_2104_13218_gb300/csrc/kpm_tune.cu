@@ -1,7 +1,7 @@
 // Autotuner of the moment loop (the paper has no counterpart): a search over
 // the choices that change only the schedule of the Chebyshev step, not its
 // arithmetic beyond the order of the sums:
-//   - neighbour-list kernel or matrix-free kernel (where lists apply),
+//   - neighbour-list, hi-block or matrix-free kernel (where they apply),
 //   - states per tile,
 //   - resident blocks per SM of the persistent grid,
 //   - FP32 rows of 17..32 chunks as two states per warp or one,
@@ -49,16 +49,17 @@ std::string problem_key(const kpm_model *m, int n_sectors, const int32_t *n_up, 
   return k;
 }
 
-void describe(const Knobs &kn, bool lists, char *out, size_t len) {
+void describe(const Knobs &kn, bool lists, bool block, char *out, size_t len) {
   snprintf(out, len, "kernel=%s tile_states=%lld blocks_per_sm=%d two_state=%d side_min_dim=%lld",
-           lists ? "list" : "matrix-free", (long long)kn.tile_states, kn.blocks_per_sm,
-           kn.two_state, (long long)kn.side_min_dim);
+           block ? "hi-block" : (lists ? "list" : "matrix-free"), (long long)kn.tile_states,
+           kn.blocks_per_sm, kn.two_state, (long long)kn.side_min_dim);
 }
 
 // Times one candidate: init, 1 + steps matrix-vector products and assembly.
 int time_candidate(const kpm_model *m, int n_sectors, const int32_t *n_up, const double *a,
                    const double *b, int R, int precision, int steps, const Knobs &kn,
-                   cudaStream_t s, double *ms, bool *uses_lists, Knobs *resolved) {
+                   cudaStream_t s, double *ms, bool *uses_lists, Knobs *resolved,
+                   bool *uses_block = nullptr) {
   MomentsJob job;
   const int K = 2 * (steps + 1);
   KPM_TRY(prepare_job(m, n_sectors, n_up, K, R, precision, &job, kn));
@@ -92,6 +93,7 @@ int time_candidate(const kpm_model *m, int n_sectors, const int32_t *n_up, const
   cudaEventDestroy(e1);
   *ms = best;
   if (uses_lists) *uses_lists = job.has_main && job.main.list_stride > 0;
+  if (uses_block) *uses_block = job.has_main && job.main.block_L > 0;
   if (resolved) {
     *resolved = kn;
     if (job.has_main) resolved->tile_states = job.main.plan.tile_states;
@@ -132,17 +134,23 @@ extern "C" int kpm_autotune(const kpm_model *model, int32_t n_sectors, const int
   KPM_TRY(time_candidate(model, n_sectors, n_up, a, b, R, precision, trial_steps, best, s, &t_def,
                          &lists, &resolved));
   const int64_t ts0 = resolved.tile_states;
+  bool uses_block = false;
+  {
+    MomentsJob probe;
+    if (prepare_job(model, n_sectors, n_up, 2, R, precision, &probe) == KPM_OK)
+      uses_block = probe.has_main && probe.main.block_L > 0;
+  }
   double t_best = t_def;
   std::string log;
   char line[256];
   auto consider = [&](const Knobs &cand) -> int {
     double t = 0.0;
-    bool l = false;
+    bool l = false, bk = false;
     int rc = time_candidate(model, n_sectors, n_up, a, b, R, precision, trial_steps, cand, s, &t,
-                            &l, nullptr);
+                            &l, nullptr, &bk);
     if (rc == KPM_ENOMEM) return KPM_OK;  // a candidate that does not fit is skipped
     KPM_TRY(rc);
-    describe(cand, l, line, sizeof(line));
+    describe(cand, l, bk, line, sizeof(line));
     log += line;
     snprintf(line, sizeof(line), ": %.4f ms\n", t);
     log += line;
@@ -156,6 +164,11 @@ extern "C" int kpm_autotune(const kpm_model *model, int32_t n_sectors, const int
   if (lists) {
     Knobs c = best;
     c.lists = 0;
+    KPM_TRY(consider(c));
+  }
+  if (uses_block) {
+    Knobs c = best;
+    c.block = 0;
     KPM_TRY(consider(c));
   }
   // 2. states per tile
@@ -199,14 +212,14 @@ extern "C" int kpm_autotune(const kpm_model *model, int32_t n_sectors, const int
   if (default_ms) *default_ms = t_def / (trial_steps + 1);
   if (best_ms) *best_ms = t_best / (trial_steps + 1);
   if (report && report_len > 0) {
-    bool l_best = false;
-    double dummy = 0.0;
+    bool l_best = false, b_best = false;
     // the kernel the best choice resolves to
     MomentsJob job;
-    if (prepare_job(model, n_sectors, n_up, 2, R, precision, &job, best) == KPM_OK)
+    if (prepare_job(model, n_sectors, n_up, 2, R, precision, &job, best) == KPM_OK) {
       l_best = job.has_main && job.main.list_stride > 0;
-    (void)dummy;
-    describe(best, l_best, line, sizeof(line));
+      b_best = job.has_main && job.main.block_L > 0;
+    }
+    describe(best, l_best, b_best, line, sizeof(line));
     std::string out = std::string("best: ") + line + "\n" + log;
     snprintf(report, report_len, "%s", out.c_str());
   }

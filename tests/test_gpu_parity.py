@@ -115,6 +115,21 @@ def test_sawtooth_all_sectors(precision, tol):
     _check_moments(gpu, ref, n_up, model, tol)
 
 
+@pytest.mark.parametrize("precision,R", [("fp32", 1), ("fp32", 4), ("fp64", 1), ("fp64", 2)])
+def test_hi_block_kernel_sector_runs(precision, R):
+    """Sector runs whose rows are one 16-byte chunk go through the hi-block kernel (low bonds
+    from shared memory, high bonds as whole partner blocks, cross bonds gathered): ragged
+    sectors including one-state ones, several bond geometries, against the oracle."""
+    tol = TOL64 if precision == "fp64" else TOL32
+    cases = [(W.ring(16), [8, 7, 3, 0, 16, 1]), (W.j1j2_chain(14, 1.0, 0.45), W.all_sectors(14)),
+             (W.sawtooth(14, -1.0, 0.45), [7, 6, 9]), (W.ladder(14), [7, 5])]
+    for model, n_up in cases:
+        a, b = _exact_bounds(model, n_up, 0.025)
+        gpu = kpm.moments(model, n_up, 48, R, 13, a=a, b=b, r0=5, precision=precision)
+        ref = _oracle_runs(model, n_up, a, b, 48, R, 13, r0=5)
+        _check_moments(gpu, ref, n_up, model, tol)
+
+
 def test_many_tiles_and_ragged_tail():
     """A sector spanning many tiles with a ragged last tile (N = 16, k = 7: 11440 states)."""
     model = W.j1j2_chain(16, 1.0, 0.4)
