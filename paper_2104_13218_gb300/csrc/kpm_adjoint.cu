@@ -52,6 +52,14 @@ struct AdjArgs {
   int pstride;         // entries per tile in gpart
   int cstart[kMaxClasses + 1];
   double half_n;
+  // neighbour lists of the forward run (list path): per state a header with
+  // the anti-aligned bond count of each coupling group, then the first chunk
+  // of every flipped neighbour's row, group by group; every group lies in one
+  // parameter class gclass[g], which has nbclass[p] bonds in all
+  const uint32_t *lists;
+  int list_stride;
+  int gclass[kMaxGroups];
+  int nbclass[kMaxClasses];
 };
 
 __device__ __forceinline__ double cot_at(const double *g, int sec, int K, int i) {
@@ -330,6 +338,163 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The same step driven by the forward run's neighbour lists (coupling groups
+// that each lie in one parameter class): the flipped neighbours' rows come from
+// the list instead of bond tests and ranks, which every lane of a state would
+// otherwise repeat.
+template <int CPL, bool FULL>
+__global__ void __launch_bounds__(kThreads)
+    adjoint_list_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ BondsDev bd) {
+  using V = double2;
+  __shared__ double s_red[kWarps * kMaxClasses];
+  __shared__ int s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = a.G_lanes;
+  const int grp = lane / G, sub = lane - grp * G;
+  const bool active = grp < a.gpw;
+  const int64_t crow = a.Rp / 2;
+  const int ng = bd.n_groups;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= a.tb.n_tiles) break;
+    const Tile tile = a.tb.tiles[t];
+    const SectorDev sd = a.tb.sectors[tile.sector];
+    const int sec = tile.sector;
+    const int n = a.n;
+    double w4[3], w2p[3], wc[3];
+    for (int q = 0; q < 3; ++q) {
+      w4[q] = 4.0 * cot_at(a.G[q], sec, a.K, 2 * n);
+      w2p[q] = 2.0 * cot_at(a.G[q], sec, a.K, 2 * n + 1);
+      wc[q] = (n >= 2) ? 2.0 * cot_at(a.G[q], sec, a.K, 2 * n - 1) : a.hbar[sec * 3 + q];
+    }
+    const double A = 2.0 * sd.inv_a;
+    const bool full_tile = sd.n_up < 0;
+    double acc[kMaxClasses];
+#pragma unroll
+    for (int p = 0; p < kMaxClasses; ++p) acc[p] = 0.0;
+    if (active) {
+      for (uint32_t u = warp * a.gpw + grp; u < tile.count; u += kWarps * a.gpw) {
+        const int64_t row = tile.row0 + u;
+        const double M = full_tile ? (double)__popcll((uint64_t)(row - sd.row0)) - a.half_n : sd.Mval;
+        const double c4 = w4[0] + M * (w4[1] + M * w4[2]);
+        const double c2p = w2p[0] + M * (w2p[1] + M * w2p[2]);
+        const double cm = wc[0] + M * (wc[1] + M * wc[2]);
+        if (a.mode == 0) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const V v = a.Vg[row * crow + sub + c * G];
+            a.Lo[row * crow + sub + c * G] = make_double2(cm * v.x, cm * v.y);
+          }
+          continue;
+        }
+        const uint32_t *Ls = a.lists + (size_t)row * a.list_stride;
+        const uint32_t hdr = __ldg(Ls);
+        V vn[CPL], lg[CPL], hv[CPL], hl[CPL];
+        double own = 0.0;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int64_t idx = row * crow + sub + c * G;
+          vn[c] = a.Vg[idx];
+          lg[c] = a.Lg[idx];
+          own = fma(vn[c].x, lg[c].x, fma(vn[c].y, lg[c].y, own));
+          hv[c] = make_double2(0.0, 0.0);
+          hl[c] = make_double2(0.0, 0.0);
+        }
+        double d = bd.J_quarter_sum;
+        double tnb[kMaxClasses];
+        int anti[kMaxClasses];
+#pragma unroll
+        for (int p = 0; p < kMaxClasses; ++p) {
+          tnb[p] = 0.0;
+          anti[p] = 0;
+        }
+        int e = 1;
+#pragma unroll
+        for (int g = 0; g < kMaxGroups; ++g) {
+          if (g < ng) {
+            const int cnt = (int)((hdr >> (8 * g)) & 255u);
+            const double jh = 0.5 * bd.gJ[g];
+            d -= cnt * jh;
+            // the group's neighbour rows are summed first; the coupling and the
+            // dot product with v_n(s) are applied once per group
+            V sl[CPL], sv[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              sl[c] = make_double2(0.0, 0.0);
+              sv[c] = make_double2(0.0, 0.0);
+            }
+            for (int i = 0; i < cnt; ++i) {
+              const uint32_t ci = __ldg(Ls + e + i);
+#pragma unroll
+              for (int c = 0; c < CPL; ++c) {
+                const V l = __ldg(a.Lg + ci + sub + c * G);
+                sl[c].x += l.x;
+                sl[c].y += l.y;
+                if (a.mode == 1) {
+                  const V v = __ldg(a.Vg + ci + sub + c * G);
+                  sv[c].x += v.x;
+                  sv[c].y += v.y;
+                }
+              }
+            }
+            e += cnt;
+            double tg = 0.0;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              hl[c].x = fma(jh, sl[c].x, hl[c].x);
+              hl[c].y = fma(jh, sl[c].y, hl[c].y);
+              hv[c].x = fma(jh, sv[c].x, hv[c].x);
+              hv[c].y = fma(jh, sv[c].y, hv[c].y);
+              tg = fma(vn[c].x, sl[c].x, fma(vn[c].y, sl[c].y, tg));
+            }
+            const int pg = a.gclass[g];
+#pragma unroll
+            for (int p = 0; p < kMaxClasses; ++p) {
+              if (p == pg) {
+                tnb[p] += tg;
+                anti[p] += cnt;
+              }
+            }
+          }
+        }
+        if (a.mode == 1) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            const int64_t idx = row * crow + sub + c * G;
+            const V vp = a.Vo[idx];  // v_{n+1}
+            V vm;                    // v_{n-1} = A (H - b) v_n - v_{n+1}
+            vm.x = A * (fma(d, vn[c].x, hv[c].x) - sd.b * vn[c].x) - vp.x;
+            vm.y = A * (fma(d, vn[c].y, hv[c].y) - sd.b * vn[c].y) - vp.y;
+            a.Vo[idx] = vm;
+            V lz = make_double2(0.0, 0.0);
+            if (!a.lz_zero) lz = a.Lo[idx];
+            V ln;
+            ln.x = c4 * vn[c].x + c2p * vp.x + cm * vm.x + A * (fma(d, lg[c].x, hl[c].x) - sd.b * lg[c].x) - lz.x;
+            ln.y = c4 * vn[c].y + c2p * vp.y + cm * vm.y + A * (fma(d, lg[c].y, hl[c].y) - sd.b * lg[c].y) - lz.y;
+            a.Lo[idx] = ln;
+          }
+        }
+        // per class: sum over its bonds of <v_n(s), lambda(s ^ mask)>/2 (anti-aligned)
+        // and +-own/4 (aligned / anti-aligned)
+#pragma unroll
+        for (int p = 0; p < kMaxClasses; ++p)
+          acc[p] += 0.5 * tnb[p] + 0.25 * (a.nbclass[p] - 2 * anti[p]) * own;
+      }
+    }
+    if (a.mode != 0) {
+      block_sum<kMaxClasses>(acc, s_red);
+      if (threadIdx.x == 0) {
+        const double f = (a.mode == 2 ? 1.0 : 2.0) * sd.inv_a;
+        for (int p = 0; p < a.n_classes; ++p) a.gpart[(int64_t)t * a.pstride + p] += f * acc[p];
+      }
+    } else {
+      __syncthreads();
+    }
+  }
+}
+
 // hbar[s][q] = gbar^q_1 - sum_{j>=1} gbar^q_{2j+1}
 __global__ void adjoint_hbar_kernel(const double *g0, const double *g1, const double *g2,
                                     double *hbar, int S, int K) {
@@ -379,6 +544,16 @@ void *pick_adj_bonds(int cpl) {
     case 4: return adjb_ptr<4>();
     default: return adjb_ptr<8>();
   }
+}
+
+template <int CPL, bool FULL>
+void *adjl_ptr() {
+  return reinterpret_cast<void *>(&adjoint_list_kernel<CPL, FULL>);
+}
+
+void *pick_adj_list(int cpl, bool full) {
+  if (cpl == 1) return full ? adjl_ptr<1, true>() : adjl_ptr<1, false>();
+  return full ? adjl_ptr<2, true>() : adjl_ptr<2, false>();
 }
 
 void *pick_adj(int cpl, bool full) {
@@ -573,7 +748,30 @@ int backward_impl(const kpm_model *model, const int32_t *bond_class, int32_t n_c
   ar.pstride = ap.pstride;
   for (int p = 0; p <= kMaxClasses; ++p) ar.cstart[p] = ap.cstart[p];
   ar.half_n = 0.5 * run.plan.N;
-  void *fn = ap.by_bond ? pick_adj_bonds(run.lay.cpl) : pick_adj(run.lay.cpl, run.plan.any_full);
+  // list path: the forward run has neighbour lists (at most 2 chunks per lane)
+  // and every coupling group lies in one parameter class
+  bool use_lists = !ap.by_bond && run.list_stride > 0 && run.lists != nullptr &&
+                   (run.lay.cpl == 1 || run.lay.cpl == 2) && run.bonds.n_groups > 0;
+  if (use_lists) {
+    for (int p = 0; p < kMaxClasses; ++p)
+      ar.nbclass[p] = p < ap.n_classes ? ap.cstart[p + 1] - ap.cstart[p] : 0;
+    for (int g = 0; g < run.bonds.n_groups && use_lists; ++g) {
+      int pg = -1;
+      for (int k = run.bonds.gstart[g]; k < run.bonds.gstart[g + 1]; ++k) {
+        const int b = run.bonds.order[k];  // index into the class-sorted bond list
+        int p = 0;
+        while (p + 1 <= ap.n_classes && ap.cstart[p + 1] <= b) ++p;
+        if (pg < 0) pg = p;
+        if (p != pg) use_lists = false;
+      }
+      ar.gclass[g] = pg;
+    }
+    ar.lists = run.lists;
+    ar.list_stride = run.list_stride;
+  }
+  void *fn = ap.by_bond ? pick_adj_bonds(run.lay.cpl)
+                        : (use_lists ? pick_adj_list(run.lay.cpl, run.plan.any_full)
+                                     : pick_adj(run.lay.cpl, run.plan.any_full));
   const size_t smem = ap.by_bond ? (size_t)kWarps * std::max(1, model->n_bonds) * sizeof(double) : 0;
   int per_sm = 0;
   KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
