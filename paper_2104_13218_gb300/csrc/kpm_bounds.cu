@@ -3,13 +3,14 @@
 //
 // All sectors run together: one Lanczos sequence per sector, its vectors
 // stored as 2-value rows (16 bytes per state, the second value unused) in the
-// same stacked layout as the moment loop.  Each
-// iteration is three kernels:
-//   w = H q_j - beta_j q_{j-1}  (written over q_{j-1}),  alpha_j = <w, q_j>
-//   w -= alpha_j q_j,  beta_{j+1} = |w|
-//   q_{j+1} = w / beta_{j+1}
+// same stacked layout as the moment loop.  Each iteration is two kernels:
+//   q_j = x_j / |x_j|,  w = H q_j - beta_j q_{j-1}  (written over q_{j-1}),
+//   alpha_j = <w, q_j>;
+//   x_{j+1} = w - alpha_j q_j,  beta_{j+1} = |x_{j+1}|,
 // with per-tile partial sums reduced in tile order by the last block of each
-// kernel.  The host then finds the extreme eigenvalues of each tridiagonal
+// kernel.  With grouped couplings (and lists of at most 2 GiB) the product
+// reads per-state neighbour lists built once; otherwise it ranks the flipped
+// states on the fly.  The host then finds the extreme eigenvalues of each tridiagonal
 // matrix by Sturm-sequence bisection and widens them by the residual bound
 // |beta_{m+1} y_m| of the Ritz pair (y the Ritz vector of the tridiagonal
 // matrix), which brackets an eigenvalue of H.
@@ -27,19 +28,34 @@ constexpr int kMaxLanczos = 1000;
 // uniform in (-1, 1) (such a vector is orthogonal to no eigenvector with
 // probability one).  Rows keep two values so that they are 16 bytes wide.
 constexpr int kLanczosColumns = 1;
+// Neighbour rows loaded together by the Lanczos product.
+constexpr int kLanczosBatch = 8;
 
 struct LanczosArgs {
-  double2 *P;        // q_{j-1} in, w out (kernel 1); w (kernel 2, 3)
-  const double2 *Q;  // q_j
+  double2 *X;        // x_j = beta_j q_j, unnormalised (mode 1: read; mode 2: x_{j+1} written)
+  double2 *P;        // mode 1: q_{j-1} in, w out; mode 2: w in
+  double2 *Q;        // mode 1: q_j out; mode 2: q_j in
   TablesDev tb;
+  const uint32_t *lists;  // entry-major neighbour lists (row indices), or null: ranks on the fly
+  uint64_t list_estride;  // word offset between a state's entries
   double *partials;  // [n_tiles][2]
-  double *coef;      // kernel 1: beta_j per [sector][2]; kernel 2: alpha_j; kernel 3: beta_{j+1}
-  double *out;       // kernel 1: alpha_j [sector][2]; kernel 2: beta_{j+1}
+  const double *nrm; // |x_j| per [sector][2] (mode 1)
+  const double *sub; // coefficient of q_{j-1} per [sector][2] (mode 1; 0 for j = 0)
+  const double *alp; // alpha_j per [sector][2] (mode 2)
+  double *out;       // mode 0: |x_0|; mode 1: alpha_j; mode 2: beta_{j+1}
   int *queue, *done;
-  int mode;          // 1 = matvec, 2 = orthogonalise, 3 = normalise
+  int mode;          // 0 = |x_0|, 1 = matrix-vector product, 2 = orthogonalise
   double breakdown;  // beta below this ends a sequence
 };
 
+// One Lanczos half-iteration over all sectors, one state per thread:
+//   mode 1: q_j = x_j / |x_j| (written), w = H q_j - beta_j q_{j-1} (written over
+//           q_{j-1}), alpha_j = <w, q_j>;
+//   mode 2: x_{j+1} = w - alpha_j q_j (written), beta_{j+1} = |x_{j+1}|;
+//   mode 0: |x_0|.
+// The normalisation of x_j is folded into the next product, so that an
+// iteration takes two passes.  Per-tile partial sums are reduced in tile order
+// by the last block.
 __global__ void __launch_bounds__(kThreads)
     lanczos_kernel(const __grid_constant__ LanczosArgs a, const __grid_constant__ BondsDev bd) {
   __shared__ double s_red[kWarps * 2];
@@ -52,52 +68,96 @@ __global__ void __launch_bounds__(kThreads)
     if (t >= a.tb.n_tiles) break;
     const Tile tile = a.tb.tiles[t];
     const SectorDev sd = a.tb.sectors[tile.sector];
-    const double c0 = a.coef[tile.sector * 2];
     double acc[2] = {0.0, 0.0};
     uint32_t hb = tile.b_first;
-    // one state per thread, consecutive states on consecutive lanes
-    for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
-      const int64_t row = tile.row0 + u;
-      if (a.mode == 1) {
-        uint64_t s;
-        if (sd.n_up < 0)
-          s = (uint64_t)(row - sd.row0);
-        else
-          s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+    if (a.mode == 1) {
+      const double n = a.nrm[tile.sector * 2];
+      const double sc = n > 0.0 ? 1.0 / n : 0.0;
+      const double c = a.sub[tile.sector * 2];
+      for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
+        const int64_t row = tile.row0 + u;
         double d = bd.J_quarter_sum;
         double h0 = 0.0;
-        for (int b = 0; b < bd.n_bonds; ++b) {
-          const uint64_t m = bd.mask[b];
-          const uint64_t tt = s & m;
-          if (tt != 0 && tt != m) {
-            d -= 0.5 * bd.J[b];
-            const uint64_t f = s ^ m;
-            const int64_t nr = sd.row0 + (sd.n_up < 0 ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
-            h0 = fma(0.5 * bd.J[b], __ldg(&a.Q[nr].x), h0);
+        if (a.lists != nullptr) {
+          const uint32_t *L = a.lists + row;
+          const uint64_t es = a.list_estride;
+          const uint32_t hdr = __ldg(L);
+          int e = 1;
+          for (int g = 0; g < bd.n_groups; ++g) {
+            const int cnt = (int)((hdr >> (8 * g)) & 255u);
+            double gs = 0.0;
+            // batches of independent loads: the indices, then the rows
+            for (int k = 0; k < cnt; k += kLanczosBatch) {
+              uint32_t nb[kLanczosBatch];
+#pragma unroll
+              for (int q = 0; q < kLanczosBatch; ++q)
+                nb[q] = k + q < cnt ? __ldg(L + (uint64_t)(e + k + q) * es) : 0u;
+              double v[kLanczosBatch];
+#pragma unroll
+              for (int q = 0; q < kLanczosBatch; ++q) v[q] = k + q < cnt ? __ldg(&a.X[nb[q]].x) : 0.0;
+#pragma unroll
+              for (int q = 0; q < kLanczosBatch; ++q) gs += v[q];
+            }
+            e += cnt;
+            d -= cnt * (0.5 * bd.gJ[g]);
+            h0 = fma(0.5 * bd.gJ[g], gs, h0);
+          }
+        } else {
+          uint64_t s;
+          if (sd.n_up < 0)
+            s = (uint64_t)(row - sd.row0);
+          else
+            s = sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
+          for (int b0 = 0; b0 < bd.n_bonds; b0 += kLanczosBatch) {
+            int64_t nr[kLanczosBatch];
+#pragma unroll
+            for (int q = 0; q < kLanczosBatch; ++q) {
+              nr[q] = -1;
+              const int b = b0 + q;
+              if (b < bd.n_bonds) {
+                const uint64_t m = bd.mask[b];
+                const uint64_t tt = s & m;
+                if (tt != 0 && tt != m) {
+                  d -= 0.5 * bd.J[b];
+                  const uint64_t f = s ^ m;
+                  nr[q] = sd.row0 + (sd.n_up < 0 ? (int64_t)f : (int64_t)sector_rank(f, a.tb));
+                }
+              }
+            }
+            double v[kLanczosBatch];
+#pragma unroll
+            for (int q = 0; q < kLanczosBatch; ++q) v[q] = nr[q] >= 0 ? __ldg(&a.X[nr[q]].x) : 0.0;
+#pragma unroll
+            for (int q = 0; q < kLanczosBatch; ++q)
+              if (nr[q] >= 0) h0 = fma(0.5 * bd.J[b0 + q], v[q], h0);
           }
         }
-        const double q = a.Q[row].x;
-        const double z = a.P[row].x;
-        const double w = fma(d, q, h0) - c0 * z;
+        const double q = a.X[row].x * sc;
+        const double w = fma(d, q, h0 * sc) - c * a.P[row].x;
+        a.Q[row].x = q;
         a.P[row].x = w;
         acc[0] = fma(w, q, acc[0]);
-      } else if (a.mode == 2) {
-        const double q = a.Q[row].x;
-        const double w = a.P[row].x - c0 * q;
-        a.P[row].x = w;
+      }
+    } else if (a.mode == 2) {
+      const double al = a.alp[tile.sector * 2];
+      for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
+        const int64_t row = tile.row0 + u;
+        const double w = a.P[row].x - al * a.Q[row].x;
+        a.X[row].x = w;
         acc[0] = fma(w, w, acc[0]);
-      } else {
-        const double w = a.P[row].x;
-        a.P[row].x = c0 > 0.0 ? w / c0 : 0.0;
+      }
+    } else {
+      for (uint32_t u = threadIdx.x; u < tile.count; u += kThreads) {
+        const double x = a.X[tile.row0 + u].x;
+        acc[0] = fma(x, x, acc[0]);
       }
     }
     block_sum<2>(acc, s_red);
-    if (threadIdx.x == 0 && a.mode != 3) {
+    if (threadIdx.x == 0) {
       a.partials[(int64_t)t * 2] = acc[0];
       a.partials[(int64_t)t * 2 + 1] = acc[1];
     }
   }
-  if (a.mode == 3) return;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1) == (int)gridDim.x - 1);
@@ -194,13 +254,32 @@ int sm_count_b() {
 
 struct BoundsLayout {
   MomentsRun run;    // plan with R = 2 FP64 rows
+  int list_stride = 0;  // > 0: the product reads neighbour lists of this many entries
+  uint64_t list_estride = 0;  // entry-major lists: word offset between entries
+  size_t list_bytes = 0;
   size_t bytes = 0;
 };
+
+// Neighbour lists of the Lanczos product (grouped couplings; at most this many
+// bytes, beyond which the ranks are computed on the fly).
+constexpr size_t kBoundsListMaxBytes = (size_t)2 << 30;
 
 int prepare_bounds(const kpm_model *m, int n_sectors, const int32_t *n_up, BoundsLayout *bl) {
   KPM_TRY(prepare_run(m, n_sectors, n_up, 2, 2, KPM_FP64, &bl->run));
   const MomentsRun &r = bl->run;
-  bl->bytes = 2 * r.vec_bytes + tables_bytes(r.plan) +
+  bl->list_stride = 0;
+  bl->list_estride = 0;
+  bl->list_bytes = 0;
+  if (r.bonds.n_groups > 0 && m->n_bonds <= 255 && r.plan.total_rows < ((int64_t)1 << 32)) {
+    const uint64_t es = (uint64_t)(r.plan.total_rows + 63) / 64 * 64;
+    const size_t lb = align256((size_t)es * (1 + m->n_bonds) * sizeof(uint32_t));
+    if (lb <= kBoundsListMaxBytes) {
+      bl->list_stride = 1 + m->n_bonds;
+      bl->list_estride = es;
+      bl->list_bytes = lb;
+    }
+  }
+  bl->bytes = 3 * r.vec_bytes + bl->list_bytes + tables_bytes(r.plan) +
               align256(std::max<size_t>(1, r.plan.tiles.size()) * 2 * sizeof(double)) +
               2 * align256((size_t)(kMaxLanczos + 1) * n_sectors * 2 * sizeof(double)) +
               align256((size_t)4 * (kMaxLanczos + 2) * sizeof(int)) +
@@ -237,15 +316,18 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   Workspace ws;
   KPM_TRY(ws.acquire(workspace, ws_bytes, bl.bytes, stream));
   Arena arena{reinterpret_cast<char *>(ws.ptr), ws.size, 0};
+  double2 *X = arena.take<double2>(r.vec_bytes / sizeof(double2));
   double2 *P = arena.take<double2>(r.vec_bytes / sizeof(double2));
   double2 *Q = arena.take<double2>(r.vec_bytes / sizeof(double2));
+  uint32_t *lists = bl.list_stride > 0 ? arena.take<uint32_t>(bl.list_bytes / sizeof(uint32_t)) : nullptr;
   double *partials = arena.take<double>(std::max<size_t>(1, r.plan.tiles.size()) * 2);
   const size_t nab = (size_t)(kMaxLanczos + 1) * n_sectors * 2;
   double *alpha = arena.take<double>(nab);
   double *beta = arena.take<double>(nab);
   int *counters = arena.take<int>((size_t)4 * (kMaxLanczos + 2));
   double *norm0 = arena.take<double>((size_t)n_sectors * 2);
-  KPM_REQUIRE(P && Q && partials && alpha && beta && counters && norm0, KPM_ENOMEM,
+  KPM_REQUIRE(X && P && Q && partials && alpha && beta && counters && norm0 &&
+                  (bl.list_stride == 0 || lists), KPM_ENOMEM,
               "workspace too small for kpm_bounds");
   std::vector<SectorDev> sec(n_sectors);
   for (int i = 0; i < n_sectors; ++i) {
@@ -261,11 +343,13 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   KPM_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4 * (kMaxLanczos + 2), stream));
   KPM_CUDA(cudaMemsetAsync(beta, 0, sizeof(double) * nab, stream));
   KPM_CUDA(cudaMemsetAsync(alpha, 0, sizeof(double) * nab, stream));
-  // q_0: uniform random values (a vector of +-1 signs can be exactly orthogonal
-  // to an eigenvector in a small sector), two sequences per sector, normalised
-  // below by the kernels' own |w| / scale passes (modes 2 and 3 with alpha = 0).
-  KPM_TRY(launch_init(r, P, seed, 0, stream, true));
-  KPM_CUDA(cudaMemsetAsync(Q, 0, r.vec_bytes, stream));
+  // x_0: uniform random values (a vector of +-1 signs can be exactly orthogonal
+  // to an eigenvector in a small sector); q_{-1} = 0
+  KPM_TRY(launch_init(r, X, seed, 0, stream, true));
+  KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));
+  if (lists)
+    KPM_TRY(launch_build_lists(r.tb, r.bonds, (int64_t)r.plan.tiles.size(), lists, bl.list_stride,
+                               1, 1, 0, stream, bl.list_estride));
 
   double jabs = 0.0;
   for (int b = 0; b < model->n_bonds; ++b) jabs += std::fabs(model->J[b]);
@@ -273,58 +357,72 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
   KPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kThreads, 0));
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * sm_count_b(), (int64_t)r.plan.tiles.size()));
-  LanczosArgs la;
+  LanczosArgs la{};
   la.tb = r.tb;
+  la.lists = lists;
+  la.list_estride = bl.list_estride;
   la.partials = partials;
   la.breakdown = 0.0;
-  // normalise the start vectors: norm0 = |P| (mode 2 with zero alpha), P /= norm0 (mode 3)
-  for (int mode = 2; mode <= 3; ++mode) {
-    la.P = P;
-    la.Q = Q;
+  auto launch = [&](int mode, int *queue) -> int {
     la.mode = mode;
-    la.queue = counters + 4 * (kMaxLanczos + 1) + (mode == 2 ? 0 : 2);
-    la.done = la.queue + 1;
-    la.coef = mode == 2 ? beta : norm0;  // beta[0 .. n_sectors*2) is zero here
-    la.out = norm0;
+    la.queue = queue;
+    la.done = queue + 1;
     void *args[] = {(void *)&la, (void *)&r.bonds};
     KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
     count_launches(1);
-  }
-  std::swap(P, Q);  // Q = q_0
-  KPM_CUDA(cudaMemsetAsync(P, 0, r.vec_bytes, stream));  // q_{-1} = 0
+    return KPM_OK;
+  };
+  // |x_0|
+  la.X = X;
+  la.out = norm0;
+  KPM_TRY(launch(0, counters + 4 * (kMaxLanczos + 1)));
   la.breakdown = 1e-12 * std::max(1.0, jabs);
   // Iterations run in chunks; after each chunk the host reads alpha and beta
-  // and stops once every sector's extreme Ritz values meet tol.
+  // and stops once every sector's extreme Ritz values meet tol.  beta_0 = 0
+  // (the memset above): the first product subtracts nothing.  The next chunk
+  // is queued before the host checks the last one, so that the check overlaps
+  // it; a chunk queued after convergence only writes alpha, beta entries that
+  // are not read, and the result is the same as without the overlap.
   constexpr int kChunk = 16;
   std::vector<double> h_alpha(nab), h_beta(nab);
   std::vector<double> lo_s(n_sectors), hi_s(n_sectors), worst_s(n_sectors);
+  int queued = 0;  // iterations queued on the stream
+  auto enqueue_chunk = [&]() -> int {
+    const int end = std::min(queued + kChunk, (int)max_iter);
+    for (int j = queued; j < end; ++j) {
+      // mode 1: q_j = x_j / |x_j| into Q, w = H q_j - beta_j q_{j-1} over P, alpha_j
+      la.X = X;
+      la.P = P;
+      la.Q = Q;
+      la.nrm = j == 0 ? norm0 : beta + (size_t)j * n_sectors * 2;
+      la.sub = beta + (size_t)j * n_sectors * 2;
+      la.out = alpha + (size_t)j * n_sectors * 2;
+      KPM_TRY(launch(1, counters + 4 * j));
+      // mode 2: x_{j+1} = w - alpha_j q_j into X, beta_{j+1} = |x_{j+1}|
+      la.alp = alpha + (size_t)j * n_sectors * 2;
+      la.out = beta + (size_t)(j + 1) * n_sectors * 2;
+      KPM_TRY(launch(2, counters + 4 * j + 2));
+      std::swap(P, Q);  // P = q_j (the next q_{j-1}); Q is free for q_{j+1}
+    }
+    queued = end;
+    return KPM_OK;
+  };
+  cudaEvent_t copied;
+  KPM_CUDA(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+  struct EventGuard {
+    cudaEvent_t e;
+    ~EventGuard() { cudaEventDestroy(e); }
+  } copied_guard{copied};
+  KPM_TRY(enqueue_chunk());
   int done_iters = 0;
   for (;;) {
-    const int chunk = std::min(kChunk, max_iter - done_iters);
-    for (int j = done_iters; j < done_iters + chunk; ++j) {
-      for (int mode = 1; mode <= 3; ++mode) {
-        la.P = P;
-        la.Q = Q;
-        la.mode = mode;
-        la.queue = counters + 4 * j + (mode == 1 ? 0 : (mode == 2 ? 2 : 0));
-        la.done = la.queue + 1;
-        if (mode == 3) la.queue = counters + 4 * kMaxLanczos;  // reset below
-        la.coef = mode == 1 ? beta + (size_t)j * n_sectors * 2
-                            : (mode == 2 ? alpha + (size_t)j * n_sectors * 2
-                                         : beta + (size_t)(j + 1) * n_sectors * 2);
-        la.out = mode == 1 ? alpha + (size_t)j * n_sectors * 2 : beta + (size_t)(j + 1) * n_sectors * 2;
-        if (mode == 3) KPM_CUDA(cudaMemsetAsync(la.queue, 0, sizeof(int) * 2, stream));
-        void *args[] = {(void *)&la, (void *)&r.bonds};
-        KPM_CUDA(cudaLaunchKernel((void *)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, stream));
-        count_launches(1);
-      }
-      std::swap(P, Q);  // P = q_j, Q = q_{j+1}
-    }
-    done_iters += chunk;
+    done_iters = queued;
     const size_t used = (size_t)(done_iters + 1) * n_sectors * 2;
     KPM_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * used, cudaMemcpyDeviceToHost, stream));
     KPM_CUDA(cudaMemcpyAsync(h_beta.data(), beta, sizeof(double) * used, cudaMemcpyDeviceToHost, stream));
-    KPM_CUDA(cudaStreamSynchronize(stream));
+    KPM_CUDA(cudaEventRecord(copied, stream));
+    if (queued < max_iter) KPM_TRY(enqueue_chunk());
+    KPM_CUDA(cudaEventSynchronize(copied));
     double worst_all = 0.0;
     for (int s = 0; s < n_sectors; ++s) {
       double lo = INFINITY, hi = -INFINITY, worst = 0.0;
@@ -360,6 +458,8 @@ extern "C" int kpm_bounds(const kpm_model *model, int32_t n_sectors, const int32
     }
     if (worst_all <= tol || done_iters >= max_iter) break;
   }
+  // the call returns with its stream idle (a chunk queued after convergence)
+  KPM_CUDA(cudaStreamSynchronize(stream));
 
   int status = KPM_OK;
   for (int s = 0; s < n_sectors; ++s) {

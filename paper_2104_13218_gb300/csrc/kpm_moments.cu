@@ -443,7 +443,10 @@ __global__ void __launch_bounds__(kThreads, KPM_STEP_MIN_BLOCKS)
 #define KPM_LIST_BATCH_F32_CPL1 16
 #endif
 #ifndef KPM_LIST_BATCH_F32_CPL2
-#define KPM_LIST_BATCH_F32_CPL2 4
+#define KPM_LIST_BATCH_F32_CPL2 2
+#endif
+#ifndef KPM_LIST_BATCH_F32_ONE
+#define KPM_LIST_BATCH_F32_ONE 8  // FP32 rows of one state per warp (unpadded lists)
 #endif
 #ifndef KPM_LIST_BATCH_F64
 #define KPM_LIST_BATCH_F64 4  // chunks per lane and batch (4 rows at CPL 1, 2 at CPL 2)
@@ -469,15 +472,27 @@ __host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
 #ifndef KPM_BLOCK_SMEM_KB
 #define KPM_BLOCK_SMEM_KB 48
 #endif
-// Padding unit of each group's list entries: the FP32 gather batch, 1 in FP64.
-inline int list_pad(int precision, int cpl) {
-  return precision == KPM_FP32 ? list_batch(true, cpl) : 1;
+// FP32 rows of 17..32 chunks run as two states per warp (1) or one (0) unless
+// the schedule says otherwise.
+#ifndef KPM_LIST_F32_PAD
+#define KPM_LIST_F32_PAD 1
+#endif
+#ifndef KPM_TWO_STATE_DEFAULT
+#define KPM_TWO_STATE_DEFAULT 1
+#endif
+
+// Padding unit of each group's list entries: the FP32 gather batch, except for
+// FP32 rows of one chunk per lane and one state per warp; 1 in FP64.
+inline int list_pad(int precision, int cpl, int gpw) {
+  return precision == KPM_FP32 && KPM_LIST_F32_PAD && (cpl != 1 || gpw > 1) ? list_batch(true, cpl) : 1;
 }
 
 struct ListArgs {
   uint32_t *lists;
   TablesDev tb;
-  int stride;
+  int stride;           // entries per state
+  uint64_t rstride;     // word offset between states (stride: state-major lists)
+  uint64_t estride;     // word offset between a state's entries (1: state-major)
   uint32_t crow;        // 16-byte chunks per row
   int batch;            // each group's entries are padded to a multiple of this
   uint32_t zero_chunk;  // first chunk of the all-zero row after the last state
@@ -494,7 +509,8 @@ __global__ void __launch_bounds__(kThreads)
       const int64_t row = tile.row0 + u;
       const uint64_t s = full_tile ? (uint64_t)(row - sd.row0)
                                    : sector_unrank(tile.rank0 + u, sd.n_up, tile.b_last, hb, a.tb);
-      uint32_t *L = a.lists + (size_t)row * a.stride;
+      uint32_t *L = a.lists + (size_t)row * a.rstride;
+      const uint64_t es = a.estride;
       uint32_t hdr = 0;
       int e = 1;
       for (int g = 0; g < bd.n_groups; ++g) {
@@ -505,13 +521,13 @@ __global__ void __launch_bounds__(kThreads)
           if (tt != 0 && tt != m) {
             const uint64_t f = s ^ m;
             const uint32_t rk = full_tile ? (uint32_t)f : sector_rank(f, a.tb);
-            L[e++] = ((uint32_t)sd.row0 + rk) * a.crow;
+            L[(e++) * es] = ((uint32_t)sd.row0 + rk) * a.crow;
             ++cnt;
           }
         }
         hdr |= cnt << (8 * g);
         // pad the group to whole gather batches with the zero row
-        for (uint32_t k = cnt; k % a.batch != 0; ++k) L[e++] = a.zero_chunk;
+        for (uint32_t k = cnt; k % a.batch != 0; ++k) L[(e++) * es] = a.zero_chunk;
       }
       L[0] = hdr;
     }
@@ -578,8 +594,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
   // chunk c of a lane is sub + c * G; with the two-state FP32 mapping
   // (G = 16, CPL = 2) the last slots of a row may lie past its chunks
   bool valid[CPL];
+  // chunk offsets of the gathers: a slot past the row reads the row's last
+  // chunk (ignored), so that a gather touches only the row's own cache lines
+  uint32_t coff[CPL];
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) valid[c] = (uint32_t)(sub + c * G) < crow;
+  for (int c = 0; c < CPL; ++c) {
+    valid[c] = (uint32_t)(sub + c * G) < crow;
+    coff[c] = valid[c] ? (uint32_t)(sub + c * G) : crow - 1;
+  }
   const int ng = bd.n_groups;
   const int kind = a.first ? 0 : 1;
   const T *dh_all = reinterpret_cast<const T *>(cf.diag_hi);
@@ -673,10 +695,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
               V gs[CPL];
 #pragma unroll
               for (int c = 0; c < CPL; ++c) gs[c] = V{};
-              constexpr int B = list_batch(sizeof(T) == 4, CPL);
-              if constexpr (sizeof(T) == 4) {
-                // FP32 lists pad each group to whole batches with the index of an
+              if (sizeof(T) == 4 && KPM_LIST_F32_PAD && (CPL != 1 || gpw > 1)) {
+                // FP32 lists (except rows of one chunk per lane and one state per
+                // warp) pad each group to whole batches with the index of an
                 // all-zero row, so every batch is gathered without predicates
+                constexpr int B = list_batch(true, CPL);
                 const int padded = (cnt + B - 1) / B * B;
                 for (int i = 0; i < padded; i += B) {
                   V v[B][CPL];
@@ -684,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
                   for (int q = 0; q < B; ++q) {
                     const uint32_t ci = L[e + i + q];
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + sub + c * G);
+                    for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + coff[c]);
                   }
 #pragma unroll
                   for (int q = 0; q < B; ++q) {
@@ -694,8 +717,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
                 }
                 e += padded;
               } else {
-                // FP64 lists are unpadded: the last batch is predicated (zero-row
-                // loads of 16 lanes x 16 bytes would cost more than the predicates)
+                // Unpadded lists (FP64; FP32 rows of one chunk per lane and one state
+                // per warp): the last batch is predicated.  With one state per warp
+                // the predicates are uniform over the warp and the skipped loads
+                // move no data.
+                constexpr int B = sizeof(T) == 4 ? KPM_LIST_BATCH_F32_ONE : list_batch(false, CPL);
                 for (int i = 0; i < cnt; i += B) {
                   uint32_t ci[B];
 #pragma unroll
@@ -705,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
                   for (int q = 0; q < B; ++q) {
 #pragma unroll
                     for (int c = 0; c < CPL; ++c)
-                      v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + sub + c * G) : V{};
+                      v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + coff[c]) : V{};
                   }
 #pragma unroll
                   for (int q = 0; q < B; ++q) {
@@ -1083,13 +1109,14 @@ int prepare_run(const kpm_model *m, int n_sectors, const int32_t *n_up, int K, i
     // each (the row layout in memory is unchanged; lanes whose second slot
     // lies past the row's chunks skip it), which halves the per-state work
     // of the warp.
-    if (precision == KPM_FP32 && run->lay.cpl == 1 && run->lay.G > 16 && knobs.two_state != 0) {
+    const int two_state = knobs.two_state >= 0 ? knobs.two_state : KPM_TWO_STATE_DEFAULT;
+    if (precision == KPM_FP32 && run->lay.cpl == 1 && run->lay.G > 16 && two_state != 0) {
       run->lay.G = 16;
       run->lay.cpl = 2;
       run->lay.gpw = 2;
     }
     // header word, then each group's entries (FP32: padded to whole gather batches)
-    const int B = list_pad(precision, run->lay.cpl);
+    const int B = list_pad(precision, run->lay.cpl, run->lay.gpw);
     int stride = 1;
     for (int g = 0; g < run->bonds.n_groups; ++g) {
       const int size = run->bonds.gstart[g + 1] - run->bonds.gstart[g];
@@ -1316,8 +1343,10 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
     la.lists = r.lists;
     la.tb = r.tb;
     la.stride = r.list_stride;
+    la.rstride = (uint64_t)r.list_stride;
+    la.estride = 1;
     la.crow = (uint32_t)(r.lay.Rp / r.lay.vec_width);
-    la.batch = list_pad(r.precision, r.lay.cpl);
+    la.batch = list_pad(r.precision, r.lay.cpl, r.lay.gpw);
     la.zero_chunk = (uint32_t)r.plan.total_rows * la.crow;
     const size_t row_bytes = (size_t)r.lay.Rp * r.lay.elem;
     const size_t zero_off = (size_t)r.plan.total_rows * row_bytes;  // the zero row of both vectors
@@ -1375,6 +1404,25 @@ int setup_run(MomentsRun &r, const double *a, const double *b, Arena &arena, cud
   const int64_t items = r.block_L > 0 ? (int64_t)r.plan.hb_hi.size() : (int64_t)r.plan.tiles.size();
   r.grid = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), items);
   r.grid = std::max(r.grid, 1);
+  return KPM_OK;
+}
+
+int launch_build_lists(const TablesDev &tb, const BondsDev &bd, int64_t n_tiles, uint32_t *lists,
+                       int stride, uint32_t crow, int batch, uint32_t zero_chunk, cudaStream_t s,
+                       uint64_t entry_stride) {
+  ListArgs la;
+  la.lists = lists;
+  la.tb = tb;
+  la.stride = stride;
+  la.rstride = entry_stride == 1 ? (uint64_t)stride : 1;
+  la.estride = entry_stride;
+  la.crow = crow;
+  la.batch = batch;
+  la.zero_chunk = zero_chunk;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)8 * sm_count()));
+  void *args[] = {(void *)&la, (void *)&bd};
+  KPM_CUDA(cudaLaunchKernel((void *)build_lists_kernel, dim3(grid), dim3(kThreads), args, 0, s));
+  count_launches(1);
   return KPM_OK;
 }
 

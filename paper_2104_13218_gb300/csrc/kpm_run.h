@@ -133,6 +133,14 @@ size_t run_bytes(const MomentsRun &run);
 // Carves the run's buffers from the arena and uploads tables (a, b per sector).
 int setup_run(MomentsRun &run, const double *a, const double *b, Arena &arena,
               cudaStream_t stream, const int *out_index = nullptr);
+// Neighbour lists of every state of the tables' tiles (header word of
+// per-group counts, then each group's neighbour chunks = row * crow, each
+// group padded with zero_chunk to a multiple of batch).  entry_stride 1:
+// state-major (state row's entries at row * stride + e); otherwise
+// entry-major (at e * entry_stride + row).
+int launch_build_lists(const TablesDev &tb, const BondsDev &bd, int64_t n_tiles, uint32_t *lists,
+                       int stride, uint32_t crow, int batch, uint32_t zero_chunk, cudaStream_t s,
+                       uint64_t entry_stride = 1);
 // v0 <- random vectors r0 .. r0+R-1 (padding columns zero): signs +-1/sqrt(D), or
 // with `uniform` values uniform in (-1, 1) from the same hash (Lanczos start vectors).
 int launch_init(const MomentsRun &run, void *v0, uint64_t seed, uint64_t r0, cudaStream_t s,
