@@ -58,6 +58,9 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 #ifndef KPM_BLOCK_NS
 #define KPM_BLOCK_NS 1
 #endif
+#ifndef KPM_BLOCK_HB
+#define KPM_BLOCK_HB 8  // high-bond partner rows loaded together
+#endif
 #ifndef KPM_BLOCK_MIN_BLOCKS
 #define KPM_BLOCK_MIN_BLOCKS 4
 #endif
@@ -180,24 +183,27 @@ __global__ void __launch_bounds__(kThreads, KPM_BLOCK_MIN_BLOCKS)
           V gs[NS];
 #pragma unroll
           for (int q = 0; q < NS; ++q) gs[q] = V{};
-          // high bonds: coalesced rows of the partner blocks, two at a time
+          // high bonds: coalesced rows of the partner blocks, KPM_BLOCK_HB at a
+          // time (the count is the same for the whole block: no divergence)
           const int e0 = s_hgs[g], e1 = s_hgs[g + 1];
-          int e = e0;
-          for (; e + 2 <= e1; e += 2) {
-            const int64_t o0 = s_hoff[e], o1 = s_hoff[e + 1];
-            V v0[NS], v1[NS];
+          for (int e = e0; e < e1; e += KPM_BLOCK_HB) {
+            V v[KPM_BLOCK_HB][NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-              v0[q] = __ldg(x + o0 + jj[q]);
-              v1[q] = __ldg(x + o1 + jj[q]);
+            for (int i = 0; i < KPM_BLOCK_HB; ++i) {
+              if (e + i < e1) {
+                const int64_t o = s_hoff[e + i];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v[i][q] = __ldg(x + o + jj[q]);
+              } else {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v[i][q] = V{};
+              }
             }
 #pragma unroll
-            for (int q = 0; q < NS; ++q) gs[q] = C::add(C::add(gs[q], v0[q]), v1[q]);
-          }
-          if (e < e1) {
-            const int64_t o0 = s_hoff[e];
+            for (int i = 0; i < KPM_BLOCK_HB; ++i) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) gs[q] = C::add(gs[q], __ldg(x + o0 + jj[q]));
+              for (int q = 0; q < NS; ++q) gs[q] = C::add(gs[q], v[i][q]);
+            }
           }
           // cross bonds: a row of the partner block
           for (int k = bb.cross_gs[g]; k < bb.cross_gs[g + 1]; ++k) {
