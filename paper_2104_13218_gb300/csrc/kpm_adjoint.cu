@@ -77,7 +77,6 @@ __global__ void __launch_bounds__(kThreads)
   const int grp = lane / G, sub = lane - grp * G;
   const bool active = grp < a.gpw;
   const int64_t crow = a.Rp / 2;
-  const int nb = bd.n_bonds;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -342,8 +341,18 @@ __global__ void __launch_bounds__(kThreads)
 // that each lie in one parameter class): the flipped neighbours' rows come from
 // the list instead of bond tests and ranks, which every lane of a state would
 // otherwise repeat.
+// Neighbours whose rows the list-driven adjoint loads together.
+#ifndef KPM_ADJ_BATCH
+#define KPM_ADJ_BATCH 4
+#endif
+constexpr int kAdjBatch = KPM_ADJ_BATCH;
+
+#ifndef KPM_ADJ_MIN_BLOCKS
+#define KPM_ADJ_MIN_BLOCKS 3
+#endif
+
 template <int CPL, bool FULL>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, KPM_ADJ_MIN_BLOCKS)
     adjoint_list_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ BondsDev bd) {
   using V = double2;
   __shared__ double s_red[kWarps * kMaxClasses];
@@ -371,9 +380,16 @@ __global__ void __launch_bounds__(kThreads)
     }
     const double A = 2.0 * sd.inv_a;
     const bool full_tile = sd.n_up < 0;
-    double acc[kMaxClasses];
+    // per coupling group: sums over the tile's states of <v_n(s), lambda(s ^ mask)>
+    // over the group's anti-aligned bonds, and of cnt_g * <v_n(s), lambda(s)>;
+    // and the sum of <v_n(s), lambda(s)>.  They are turned into per-class sums
+    // once per tile.
+    double acc_tg[kMaxGroups], acc_ao[kMaxGroups], acc_own = 0.0;
 #pragma unroll
-    for (int p = 0; p < kMaxClasses; ++p) acc[p] = 0.0;
+    for (int g = 0; g < kMaxGroups; ++g) {
+      acc_tg[g] = 0.0;
+      acc_ao[g] = 0.0;
+    }
     if (active) {
       for (uint32_t u = warp * a.gpw + grp; u < tile.count; u += kWarps * a.gpw) {
         const int64_t row = tile.row0 + u;
@@ -403,13 +419,7 @@ __global__ void __launch_bounds__(kThreads)
           hl[c] = make_double2(0.0, 0.0);
         }
         double d = bd.J_quarter_sum;
-        double tnb[kMaxClasses];
-        int anti[kMaxClasses];
-#pragma unroll
-        for (int p = 0; p < kMaxClasses; ++p) {
-          tnb[p] = 0.0;
-          anti[p] = 0;
-        }
+        acc_own += own;
         int e = 1;
 #pragma unroll
         for (int g = 0; g < kMaxGroups; ++g) {
@@ -425,17 +435,30 @@ __global__ void __launch_bounds__(kThreads)
               sl[c] = make_double2(0.0, 0.0);
               sv[c] = make_double2(0.0, 0.0);
             }
-            for (int i = 0; i < cnt; ++i) {
-              const uint32_t ci = __ldg(Ls + e + i);
+            // kAdjBatch neighbours at a time: their indices, then their rows, so
+            // that the loads of a batch are in flight together
+            for (int i0 = 0; i0 < cnt; i0 += kAdjBatch) {
+              uint32_t ci[kAdjBatch];
 #pragma unroll
-              for (int c = 0; c < CPL; ++c) {
-                const V l = __ldg(a.Lg + ci + sub + c * G);
-                sl[c].x += l.x;
-                sl[c].y += l.y;
-                if (a.mode == 1) {
-                  const V v = __ldg(a.Vg + ci + sub + c * G);
-                  sv[c].x += v.x;
-                  sv[c].y += v.y;
+              for (int q = 0; q < kAdjBatch; ++q) ci[q] = i0 + q < cnt ? __ldg(Ls + e + i0 + q) : 0u;
+              V l[kAdjBatch][CPL], v[kAdjBatch][CPL];
+#pragma unroll
+              for (int q = 0; q < kAdjBatch; ++q) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  const bool ok = i0 + q < cnt;
+                  l[q][c] = ok ? __ldg(a.Lg + ci[q] + sub + c * G) : make_double2(0.0, 0.0);
+                  v[q][c] = (ok && a.mode == 1) ? __ldg(a.Vg + ci[q] + sub + c * G) : make_double2(0.0, 0.0);
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < kAdjBatch; ++q) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                  sl[c].x += l[q][c].x;
+                  sl[c].y += l[q][c].y;
+                  sv[c].x += v[q][c].x;
+                  sv[c].y += v[q][c].y;
                 }
               }
             }
@@ -449,14 +472,8 @@ __global__ void __launch_bounds__(kThreads)
               hv[c].y = fma(jh, sv[c].y, hv[c].y);
               tg = fma(vn[c].x, sl[c].x, fma(vn[c].y, sl[c].y, tg));
             }
-            const int pg = a.gclass[g];
-#pragma unroll
-            for (int p = 0; p < kMaxClasses; ++p) {
-              if (p == pg) {
-                tnb[p] += tg;
-                anti[p] += cnt;
-              }
-            }
+            acc_tg[g] += tg;
+            acc_ao[g] += cnt * own;
           }
         }
         if (a.mode == 1) {
@@ -476,11 +493,20 @@ __global__ void __launch_bounds__(kThreads)
             a.Lo[idx] = ln;
           }
         }
-        // per class: sum over its bonds of <v_n(s), lambda(s ^ mask)>/2 (anti-aligned)
-        // and +-own/4 (aligned / anti-aligned)
+      }
+    }
+    // per class: sum over its bonds of <v_n(s), lambda(s ^ mask)>/2 (anti-aligned)
+    // and +-own/4 (aligned / anti-aligned)
+    double acc[kMaxClasses];
+#pragma unroll
+    for (int p = 0; p < kMaxClasses; ++p) acc[p] = 0.25 * a.nbclass[p] * acc_own;
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) {
+      if (g < ng) {
+        const int pg = a.gclass[g];
 #pragma unroll
         for (int p = 0; p < kMaxClasses; ++p)
-          acc[p] += 0.5 * tnb[p] + 0.25 * (a.nbclass[p] - 2 * anti[p]) * own;
+          if (p == pg) acc[p] += 0.5 * acc_tg[g] - 0.5 * acc_ao[g];
       }
     }
     if (a.mode != 0) {
