@@ -55,7 +55,7 @@ def parse_args():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--lanczos-iters", type=int, default=100)
-    p.add_argument("--lanczos-tol", type=float, default=1e-6,
+    p.add_argument("--lanczos-tol", type=float, default=1e-8,
                    help="relative residual bound at which the Lanczos bound estimate stops")
     p.add_argument("--no-large", action="store_true",
                    help="skip the blocks of the two largest workloads (ring N=34, 4x6 torus)")
