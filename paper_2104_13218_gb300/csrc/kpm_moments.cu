@@ -603,6 +603,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
     coff[c] = valid[c] ? (uint32_t)(sub + c * G) : crow - 1;
   }
   const int ng = bd.n_groups;
+  // per-slot base pointers of the gathers: row chunk ci of slot c is xs[c][ci]
+  const V *xs[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) xs[c] = x + coff[c];
   const int kind = a.first ? 0 : 1;
   const T *dh_all = reinterpret_cast<const T *>(cf.diag_hi);
   const T *dl_all = reinterpret_cast<const T *>(cf.diag_lo);
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
                   for (int q = 0; q < B; ++q) {
                     const uint32_t ci = L[e + i + q];
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(x + ci + coff[c]);
+                    for (int c = 0; c < CPL; ++c) v[q][c] = __ldg(xs[c] + ci);
                   }
 #pragma unroll
                   for (int q = 0; q < B; ++q) {
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
                   for (int q = 0; q < B; ++q) {
 #pragma unroll
                     for (int c = 0; c < CPL; ++c)
-                      v[q][c] = (i + q < cnt) ? __ldg(x + ci[q] + coff[c]) : V{};
+                      v[q][c] = (i + q < cnt) ? __ldg(xs[c] + ci[q]) : V{};
                   }
 #pragma unroll
                   for (int q = 0; q < B; ++q) {
