@@ -474,9 +474,6 @@ __host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
 #endif
 // FP32 rows of 17..32 chunks run as two states per warp (1) or one (0) unless
 // the schedule says otherwise.
-#ifndef KPM_LIST_F32_PAD
-#define KPM_LIST_F32_PAD 1
-#endif
 #ifndef KPM_TWO_STATE_DEFAULT
 #define KPM_TWO_STATE_DEFAULT 1
 #endif
@@ -484,7 +481,7 @@ __host__ __device__ constexpr int list_batch(bool fp32, int cpl) {
 // Padding unit of each group's list entries: the FP32 gather batch, except for
 // FP32 rows of one chunk per lane and one state per warp; 1 in FP64.
 inline int list_pad(int precision, int cpl, int gpw) {
-  return precision == KPM_FP32 && KPM_LIST_F32_PAD && (cpl != 1 || gpw > 1) ? list_batch(true, cpl) : 1;
+  return precision == KPM_FP32 && (cpl != 1 || gpw > 1) ? list_batch(true, cpl) : 1;
 }
 
 struct ListArgs {
@@ -699,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CPL == 2) ? KPM_L
               V gs[CPL];
 #pragma unroll
               for (int c = 0; c < CPL; ++c) gs[c] = V{};
-              if (sizeof(T) == 4 && KPM_LIST_F32_PAD && (CPL != 1 || gpw > 1)) {
+              if (sizeof(T) == 4 && (CPL != 1 || gpw > 1)) {
                 // FP32 lists (except rows of one chunk per lane and one state per
                 // warp) pad each group to whole batches with the index of an
                 // all-zero row, so every batch is gathered without predicates
