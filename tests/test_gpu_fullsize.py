@@ -14,7 +14,7 @@ times, against the oracle, and the FP32 form's error on the thermodynamics.
 
 The stored oracle moments come from tests/golden/make_large_sector_moments.py (the plain
 C recursion of oracle/naive_kpm.c).  The measured thermodynamic errors are written to
-gpurun_out/fp32_thermo_error.json when that folder exists.
+$KPM_RECORD_DIR/fp32_thermo_error.json when that variable names a folder.
 """
 import json
 import math
@@ -53,8 +53,8 @@ def _golden_moments(name):
 
 
 def _record(key, value):
-    out = os.path.join(ROOT, "gpurun_out")
-    if not os.path.isdir(out):
+    out = os.environ.get("KPM_RECORD_DIR", "")
+    if not out or not os.path.isdir(out):
         return
     path = os.path.join(out, "fp32_thermo_error.json")
     d = {}
