@@ -390,8 +390,8 @@ int kpm_moments_backward_ex(const kpm_model *model, const int32_t *bond_class, i
  * problem's scratch (kpm_moments_workspace_size) exceeds the array.  The
  * first call on a device looks up the array's device address with
  * cudaGetSymbolAddress while that device is current (and so does the first
- * call after the device's context was replaced, e.g. by cudaDeviceReset);
- * make that first call before any stream capture.  Like kpm_moments, every
+ * call after the device's context was replaced, e.g. by cudaDeviceReset).
+ * Like kpm_moments, every
  * call waits for `stream` before it returns (it reads the EBOUNDS flag back to
  * the host).  All calls share the array and every call clears the parts that
  * must start at zero; calls whose work overlaps on the GPU (different streams
