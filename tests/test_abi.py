@@ -1,6 +1,7 @@
 """The C ABI library loads, exports every function include/kpm.h declares, and
 rejects invalid arguments before touching the GPU (no GPU needed)."""
 import ctypes
+import math
 import os
 import re
 
@@ -88,3 +89,19 @@ def test_workspace_sizes_scale_with_problem():
     # two interleaved vectors of the ring-34 S^z = 0 sector in FP32 with R = 4
     cfg5 = kpm.moments_workspace_size(W.ring(34), [17], 2000, 4, "fp32")
     assert cfg5 >= 2 * 2333606220 * 4 * 4
+
+
+def test_bounds_workspace_holds_three_vectors_and_lists():
+    # three FP64 Lanczos vectors (16-byte rows); with grouped couplings also the
+    # entry-major neighbour lists (a header word and one word per bond and state)
+    dim = math.comb(14, 7)
+    ring = W.ring(14)
+    grouped = kpm.bounds_workspace_size(ring, [7])
+    assert grouped >= 3 * dim * 16 + dim * (1 + 14) * 4
+    # more distinct couplings than the grouped step handles: no lists
+    distinct = W.Model("ring14_distinct", 14, ring.bi, ring.bj, tuple(1.0 + 0.1 * k for k in range(14)))
+    ungrouped = kpm.bounds_workspace_size(distinct, [7])
+    assert 3 * dim * 16 <= ungrouped < grouped
+    # the ring N=34 S^z=0 sector: lists would exceed 2 GiB, so only the vectors
+    big = kpm.bounds_workspace_size(W.ring(34), [17])
+    assert 3 * 2333606220 * 16 <= big < 3 * 2333606220 * 16 + (1 << 31)
